@@ -1,0 +1,215 @@
+/*
+ * CPU oracle for the read-to-read alignment distance.  TEST INFRASTRUCTURE ONLY:
+ * it is called by the tests, by the package's smoke check and by the CPU-baseline
+ * leg of the benchmark, never by the library's compute path.  It shares no code,
+ * header or table with the CUDA library.
+ *
+ * What it computes (paper section 2.2, "Scalable pairwise distances computation"):
+ * the dissimilarity between two reads is derived from their local alignment score,
+ * computed with the Smith-Waterman algorithm, for every pair of reads (the m x n
+ * matrix D of the program `disseq`, and its all-pairs form with ~5e9 values for
+ * 1e5 reads, i.e. the strict upper triangle).
+ *
+ * The paper fixes neither the scores nor the score-to-distance conversion.  The
+ * readings used here (each one an argument, with these defaults):
+ *   substitution  s(x,y) = +1 if x == y else -1   (match = 1, mismatch = -1)
+ *   gaps          linear, -1 per gapped base      (gap = 1)
+ *   local score   H(i,0) = H(0,j) = 0,
+ *                 H(i,j) = max(0, H(i-1,j-1) + s(a_i,b_j), H(i-1,j) - g, H(i,j-1) - g),
+ *                 S = max over all cells of H   (Smith & Waterman 1981, textbook form)
+ *   distance      d = max(la, lb) - S           (stored as an unsigned 16-bit integer)
+ *   all pairs     strict upper triangle, row-major: k(i,j) = i*n - i*(i+1)/2 + (j-i-1)
+ *
+ * The implementation is the plain definition: the full (la+1) x (lb+1) matrix is
+ * allocated and filled row by row.  Bases are compared case-insensitively.
+ */
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+static int upper_base(uint8_t c) { return (c >= 'a' && c <= 'z') ? (c - 'a' + 'A') : c; }
+
+static int max2(int x, int y) { return x > y ? x : y; }
+
+/* Smith-Waterman local alignment score S, from the full DP matrix H. */
+int oracle_sw_score(const uint8_t *a, int64_t la, const uint8_t *b, int64_t lb,
+                    int match, int mismatch, int gap)
+{
+    if (la <= 0 || lb <= 0) return 0;
+    int64_t w = lb + 1;
+    int *H = (int *)malloc(sizeof(int) * (size_t)(la + 1) * (size_t)w);
+    if (!H) return -1;
+    for (int64_t j = 0; j <= lb; ++j) H[j] = 0;              /* H(0,j) = 0 */
+    int S = 0;
+    for (int64_t i = 1; i <= la; ++i) {
+        H[i * w] = 0;                                         /* H(i,0) = 0 */
+        for (int64_t j = 1; j <= lb; ++j) {
+            int s = (upper_base(a[i - 1]) == upper_base(b[j - 1])) ? match : mismatch;
+            int h = 0;
+            h = max2(h, H[(i - 1) * w + (j - 1)] + s);
+            h = max2(h, H[(i - 1) * w + j] - gap);
+            h = max2(h, H[i * w + (j - 1)] - gap);
+            H[i * w + j] = h;
+            S = max2(S, h);
+        }
+    }
+    free(H);
+    return S;
+}
+
+/* d = max(la, lb) - S, the distance reading of the score. */
+int oracle_distance(const uint8_t *a, int64_t la, const uint8_t *b, int64_t lb,
+                    int match, int mismatch, int gap)
+{
+    int S = oracle_sw_score(a, la, b, lb, match, mismatch, gap);
+    int64_t m = la > lb ? la : lb;
+    return (int)(m - S);
+}
+
+/* Position of pair (i, j), i < j, in the row-major strict upper triangle of n reads. */
+uint64_t oracle_tri_index(uint64_t i, uint64_t j, uint64_t n)
+{
+    return i * n - i * (i + 1) / 2 + (j - i - 1);
+}
+
+/* ---------------------------------------------------------------- threaded drivers */
+
+typedef struct {
+    const uint8_t *seq;
+    const uint64_t *off;
+    uint64_t n;
+    const uint8_t *seqB;      /* rect mode: second read set */
+    const uint64_t *offB;
+    uint64_t a0, a1, b0, b1, ld;
+    const uint64_t *pi, *pj;  /* pairs mode */
+    uint64_t npairs;
+    uint16_t *out;
+    int32_t *out_score;       /* pairs mode: raw scores S instead of distances */
+    int match, mismatch, gap;
+    int mode;                 /* 0 = triangle rows, 1 = pair list, 2 = rectangle rows */
+    uint64_t next;            /* shared work counter */
+} job_t;
+
+static uint64_t take(job_t *J, uint64_t chunk)
+{
+    return __atomic_fetch_add(&J->next, chunk, __ATOMIC_RELAXED);
+}
+
+static void *worker(void *arg)
+{
+    job_t *J = (job_t *)arg;
+    if (J->mode == 0) {
+        for (;;) {
+            uint64_t i = take(J, 1);
+            if (i >= J->n) break;
+            const uint8_t *a = J->seq + J->off[i];
+            int64_t la = (int64_t)(J->off[i + 1] - J->off[i]);
+            for (uint64_t j = i + 1; j < J->n; ++j) {
+                const uint8_t *b = J->seq + J->off[j];
+                int64_t lb = (int64_t)(J->off[j + 1] - J->off[j]);
+                J->out[oracle_tri_index(i, j, J->n)] =
+                    (uint16_t)oracle_distance(a, la, b, lb, J->match, J->mismatch, J->gap);
+            }
+        }
+    } else if (J->mode == 1) {
+        for (;;) {
+            uint64_t p0 = take(J, 64);
+            if (p0 >= J->npairs) break;
+            uint64_t p1 = p0 + 64 < J->npairs ? p0 + 64 : J->npairs;
+            for (uint64_t p = p0; p < p1; ++p) {
+                uint64_t i = J->pi[p], j = J->pj[p];
+                const uint8_t *a = J->seq + J->off[i];
+                const uint8_t *b = J->seqB + J->offB[j];
+                int64_t la = (int64_t)(J->off[i + 1] - J->off[i]);
+                int64_t lb = (int64_t)(J->offB[j + 1] - J->offB[j]);
+                if (J->out_score)
+                    J->out_score[p] = oracle_sw_score(a, la, b, lb, J->match, J->mismatch, J->gap);
+                else
+                    J->out[p] = (uint16_t)oracle_distance(a, la, b, lb, J->match, J->mismatch,
+                                                          J->gap);
+            }
+        }
+    } else {
+        for (;;) {
+            uint64_t r = J->a0 + take(J, 1);
+            if (r >= J->a1) break;
+            const uint8_t *a = J->seq + J->off[r];
+            int64_t la = (int64_t)(J->off[r + 1] - J->off[r]);
+            for (uint64_t c = J->b0; c < J->b1; ++c) {
+                const uint8_t *b = J->seqB + J->offB[c];
+                int64_t lb = (int64_t)(J->offB[c + 1] - J->offB[c]);
+                J->out[(r - J->a0) * J->ld + (c - J->b0)] =
+                    (uint16_t)oracle_distance(a, la, b, lb, J->match, J->mismatch, J->gap);
+            }
+        }
+    }
+    return NULL;
+}
+
+static int run(job_t *J, int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    if (!th) return -1;
+    int started = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        if (pthread_create(&th[t], NULL, worker, J) != 0) break;
+        ++started;
+    }
+    if (started == 0) worker(J);
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    free(th);
+    return 0;
+}
+
+/* All pairs i < j of one read set into the strict upper triangle out[n(n-1)/2]. */
+int oracle_all_pairs(const uint8_t *seq, const uint64_t *off, uint64_t n, uint16_t *out,
+                     int match, int mismatch, int gap, int nthreads)
+{
+    job_t J;
+    memset(&J, 0, sizeof J);
+    J.seq = seq; J.off = off; J.n = n; J.out = out;
+    J.match = match; J.mismatch = mismatch; J.gap = gap; J.mode = 0;
+    return run(&J, nthreads);
+}
+
+/* Listed pairs: out[p] = d(A[pi[p]], B[pj[p]]). */
+int oracle_pairs(const uint8_t *seqA, const uint64_t *offA, const uint8_t *seqB,
+                 const uint64_t *offB, const uint64_t *pi, const uint64_t *pj, uint64_t npairs,
+                 uint16_t *out, int match, int mismatch, int gap, int nthreads)
+{
+    job_t J;
+    memset(&J, 0, sizeof J);
+    J.seq = seqA; J.off = offA; J.seqB = seqB; J.offB = offB;
+    J.pi = pi; J.pj = pj; J.npairs = npairs; J.out = out;
+    J.match = match; J.mismatch = mismatch; J.gap = gap; J.mode = 1;
+    return run(&J, nthreads);
+}
+
+/* Listed pairs, raw local scores: out[p] = S(A[pi[p]], B[pj[p]]). */
+int oracle_pair_scores(const uint8_t *seqA, const uint64_t *offA, const uint8_t *seqB,
+                       const uint64_t *offB, const uint64_t *pi, const uint64_t *pj,
+                       uint64_t npairs, int32_t *out, int match, int mismatch, int gap,
+                       int nthreads)
+{
+    job_t J;
+    memset(&J, 0, sizeof J);
+    J.seq = seqA; J.off = offA; J.seqB = seqB; J.offB = offB;
+    J.pi = pi; J.pj = pj; J.npairs = npairs; J.out_score = out;
+    J.match = match; J.mismatch = mismatch; J.gap = gap; J.mode = 1;
+    return run(&J, nthreads);
+}
+
+/* Rectangle: out[(r-a0)*ld + (c-b0)] = d(A[r], B[c]) for r in [a0,a1), c in [b0,b1). */
+int oracle_rect(const uint8_t *seqA, const uint64_t *offA, uint64_t a0, uint64_t a1,
+                const uint8_t *seqB, const uint64_t *offB, uint64_t b0, uint64_t b1,
+                uint16_t *out, uint64_t ld, int match, int mismatch, int gap, int nthreads)
+{
+    job_t J;
+    memset(&J, 0, sizeof J);
+    J.seq = seqA; J.off = offA; J.seqB = seqB; J.offB = offB;
+    J.a0 = a0; J.a1 = a1; J.b0 = b0; J.b1 = b1; J.ld = ld; J.out = out;
+    J.match = match; J.mismatch = mismatch; J.gap = gap; J.mode = 2;
+    return run(&J, nthreads);
+}
