@@ -1,0 +1,160 @@
+/*
+ * gbd -- all-pairs Smith-Waterman read distances on one GB300 (sm_103a).
+ *
+ * The operation (arxiv 1803.02272, section 2.2, "Scalable pairwise distances
+ * computation"): the dissimilarity between two reads is derived from their local
+ * alignment score, found by the Smith-Waterman algorithm; the program `disseq` takes
+ * two read files of m and n reads and returns the m x n matrix D, and the paper's
+ * all-pairs run over 1e5 reads produces ~5e9 values (one per unordered pair).
+ *
+ * The paper fixes no scores and no score-to-distance rule.  This library's readings,
+ * all of them fields of gbd_params:
+ *   s(x,y) = +match if x == y else +mismatch (defaults +1 / -1); linear gap penalty
+ *   `gap` per gapped base (default 1);
+ *   H(i,0) = H(0,j) = 0, H(i,j) = max(0, H(i-1,j-1)+s(a_i,b_j), H(i-1,j)-gap,
+ *   H(i,j-1)-gap), S = max over all cells of H;
+ *   d = max(la, lb) - S (GBD_CONV_MAX, default), stored as uint16.
+ *
+ * Conventions for every call:
+ *   - Reads are bytes over {A,C,G,T} (lower case accepted), concatenated; read r is
+ *     seq[offsets[r] .. offsets[r+1]).  Lengths may be 0 .. 65535.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Compute calls are
+ *     asynchronous on it; gbd_load_reads synchronises `stream` once to read back its
+ *     validation flag.
+ *   - Output pointers are DEVICE pointers owned by the caller (for example a torch
+ *     tensor's data_ptr()).  The library owns gbd_ctx, gbd_set and gbd_server objects.
+ *   - Every int-returning call returns GBD_OK (0) or a GBD_E* code and then sets a
+ *     thread-local message readable with gbd_last_error().  No C++ exception crosses
+ *     this boundary.
+ *   - A context's calls may be issued from one host thread at a time; a server object
+ *     is safe to use from several host threads.
+ */
+#ifndef GBD_H
+#define GBD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GBD_OK        0
+#define GBD_EINVAL    1   /* bad argument: non-ACGT byte, length > 65535, wrong size, NULL */
+#define GBD_ENOMEM    2   /* a device or host allocation failed */
+#define GBD_EBUDGET   3   /* a request exceeds the server's HBM budget even when alone */
+#define GBD_ETIMEDOUT 4   /* a bounded wait ran out */
+#define GBD_ECUDA     5   /* a CUDA runtime call failed (message has the CUDA error) */
+#define GBD_ENOTFOUND 6   /* unknown server ticket */
+
+/* score-to-distance rules (gbd_params.conversion) */
+#define GBD_CONV_MAX   0  /* d = max(la, lb) - S, clamped to [0, 65535]  (default) */
+#define GBD_CONV_MIN   1  /* d = min(la, lb) - S, clamped to [0, 65535] */
+#define GBD_CONV_SCORE 2  /* the raw local score S, clamped to [0, 65535] */
+
+/* kernel choice (gbd_params.kernel) */
+#define GBD_KERNEL_AUTO     0  /* systolic kernel where it applies, else the general one */
+#define GBD_KERNEL_GENERAL  1  /* one pair per thread, any length and any scores */
+#define GBD_KERNEL_SYSTOLIC 2  /* warp-systolic int16x2 kernel (default scores, reads <= 512) */
+
+typedef struct gbd_ctx gbd_ctx;
+typedef struct gbd_set gbd_set;
+typedef struct gbd_server gbd_server;
+
+typedef struct {
+    int16_t  match;       /* score of a matching base pair (default +1) */
+    int16_t  mismatch;    /* score of a mismatching base pair (default -1) */
+    int16_t  gap;         /* penalty per gapped base, >= 0 (default 1) */
+    int16_t  conversion;  /* GBD_CONV_* (default GBD_CONV_MAX) */
+    int32_t  kernel;      /* GBD_KERNEL_* (default GBD_KERNEL_AUTO) */
+    uint64_t hbm_budget;  /* server admission budget in bytes; 0 = 90 % of free memory */
+    uint32_t timeout_us;  /* bound on any host wait inside the library; 0 = 60 s */
+} gbd_params;
+
+/* Fills *p with the defaults above. */
+void gbd_default_params(gbd_params *p);
+
+/* Creates a context on CUDA device `device` (made current on the calling thread).
+ * p == NULL selects the defaults.  EINVAL on a negative gap or bad enum values. */
+int gbd_create(gbd_ctx **out, int device, const gbd_params *p);
+void gbd_destroy(gbd_ctx *ctx);
+
+/* Ingest (a1): copies (if host pointers) and packs n reads into a device-resident set:
+ * 2-bit codes A=0 C=1 G=2 T=3, 16 bases per uint32 (base k of a word in bits 2k..2k+1),
+ * a fixed stride of ceil(max_len/16) words per read, and per-read uint16 lengths.
+ * `seq` and `offsets` (n+1 entries, offsets[0] may be non-zero) may both be host or both
+ * be device pointers.  EINVAL (and no set) if a byte is not A/C/G/T/a/c/g/t, a length
+ * exceeds 65535 or offsets decrease.  n == 0 gives an empty set. */
+int gbd_load_reads(gbd_ctx *ctx, const uint8_t *seq, const uint64_t *offsets, uint64_t n,
+                   gbd_set **out, void *stream);
+void gbd_free_set(gbd_set *set);
+uint64_t gbd_set_size(const gbd_set *set);           /* number of reads */
+uint32_t gbd_set_max_len(const gbd_set *set);        /* longest read */
+/* Sum over the pairs i < j of len_i * len_j: the DP cells of gbd_all_pairs. */
+double gbd_set_pair_cells(const gbd_set *set);
+
+/* All pairs (a2-a4): d_tri[k(i,j)] = d(read i, read j) for every i < j, with the
+ * row-major strict upper triangle index k(i,j) = i*n - i*(i+1)/2 + (j-i-1).
+ * tri_len must equal n(n-1)/2 (EINVAL otherwise); d_tri is a device pointer. */
+int gbd_all_pairs(gbd_ctx *ctx, const gbd_set *set, uint16_t *d_tri, uint64_t tri_len,
+                  void *stream);
+
+/* Rectangle (the m x n form of `disseq`): d_out[(r-a0)*ld + (c-b0)] = d(A[r], B[c])
+ * for r in [a0,a1), c in [b0,b1); ld >= b1-b0.  A and B may be the same set. */
+int gbd_tile(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd_set *B,
+             uint64_t b0, uint64_t b1, uint16_t *d_out, uint64_t ld, void *stream);
+
+/* Batched samples: one launch computes the all-pairs triangle of each of ns sets;
+ * d_tris[s] receives sample s's triangle (n_s(n_s-1)/2 entries, device pointers). */
+int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns,
+              uint16_t *const *d_tris, void *stream);
+
+/* Serving (a5): a resident reference set answers query batches with distance rows.
+ * submit copies the queries (host pointers, nq reads) and returns at once with a
+ * ticket; the request is admitted when its memory fits the budget beside the requests
+ * in flight, and its work overlaps theirs on the device.  d_rows (device, nq x n_ref,
+ * row-major) is complete when poll reports done or wait returns GBD_OK.
+ * EBUDGET if the request cannot fit even alone. */
+int gbd_server_create(gbd_ctx *ctx, const gbd_set *ref, gbd_server **out);
+int gbd_server_submit(gbd_server *srv, const uint8_t *seq, const uint64_t *offsets,
+                      uint64_t nq, uint16_t *d_rows, uint64_t *ticket);
+int gbd_server_poll(gbd_server *srv, uint64_t ticket, int *done);
+int gbd_server_wait(gbd_server *srv, uint64_t ticket);
+void gbd_server_destroy(gbd_server *srv);
+
+/* Thread-local text of the last error raised on the calling thread ("" if none). */
+const char *gbd_last_error(void);
+
+/* Measurement support: number of CUDA kernels this library has launched in the
+ * process so far (all contexts, all devices). */
+uint64_t gbd_kernel_launches(void);
+
+/* Measurement support: issue rate of one instruction form of the DP inner loop,
+ * in lane operations per second (op codes GBD_PROBE_*), timed with CUDA events
+ * on `stream` over `iters` iterations of a saturating kernel. */
+#define GBD_PROBE_VIMAX3_S16X2_RELU  0
+#define GBD_PROBE_VIADDMAX_S16X2     1
+#define GBD_PROBE_VIADDMAX_S16X2_RELU 2
+#define GBD_PROBE_VIMAX_S16X2_RELU   3
+#define GBD_PROBE_VMAXS2             4
+#define GBD_PROBE_PRMT               5
+#define GBD_PROBE_IADD3              6
+#define GBD_PROBE_LOP3               7
+#define GBD_PROBE_IMAX               8
+#define GBD_PROBE_HMAX2              9
+#define GBD_PROBE_HADD2              10
+#define GBD_PROBE_CELL_MIX           11
+#define GBD_PROBE_VIMAX3_S16X2       12
+#define GBD_PROBE_FMAX               13
+#define GBD_PROBE_FMAX3              14
+#define GBD_PROBE_FADD               15
+#define GBD_PROBE_MIX_DPX_HMAX2      16  /* half the chains DPX, half fp16x2 max */
+#define GBD_PROBE_MIX_DPX_FMAX3      17  /* half the chains DPX, half fp32 3-input max */
+#define GBD_PROBE_MIX_DPX_IADD3      18  /* half the chains DPX, half 3-input integer add */
+#define GBD_PROBE_COUNT              19
+int gbd_probe_op_rate(int op, uint32_t iters, double *lane_ops_per_s, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBD_H */

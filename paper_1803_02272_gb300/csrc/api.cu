@@ -1,0 +1,466 @@
+// C ABI of the library: contexts, packed read sets, and the all-pairs / rectangle /
+// batched entry points.  Serving lives in server.cu.
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "gbd_internal.cuh"
+#include "sw_systolic.cuh"
+
+namespace gbd {
+
+static thread_local std::string t_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+void set_error(const std::string &msg) { t_last_error = msg; }
+
+int fail(int code, const std::string &msg)
+{
+    set_error(msg);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    set_error(m);
+    return GBD_ECUDA;
+}
+
+static bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+Scoring scoring_of(const gbd_ctx *ctx)
+{
+    return {ctx->params.match, ctx->params.mismatch, ctx->params.gap, ctx->params.conversion};
+}
+
+static bool default_scores(const gbd_params &p) { return p.match == 1 && p.mismatch == -1 && p.gap == 1; }
+
+// The systolic kernel is specialised to the default scores.
+static bool use_systolic(const gbd_ctx *ctx)
+{
+    return ctx->params.kernel != GBD_KERNEL_GENERAL && default_scores(ctx->params);
+}
+
+// Length-sorted order of a set and its systolic entries (built once per set).
+static int build_tri_schedule(gbd_set *set, cudaStream_t st)
+{
+    TriSchedule &sc = set->sched;
+    if (sc.built) return GBD_OK;
+    const uint64_t n = set->n;
+    sc.h_perm.resize(n);
+    std::iota(sc.h_perm.begin(), sc.h_perm.end(), 0u);
+    std::stable_sort(sc.h_perm.begin(), sc.h_perm.end(),
+                     [&](uint32_t x, uint32_t y) { return set->h_len[x] < set->h_len[y]; });
+    uint64_t lb = 0;
+    while (lb < n && set->h_len[sc.h_perm[lb]] <= kSystolicMaxQuery) ++lb;
+    sc.long_begin = lb;
+    std::vector<SysEntry> entries;
+    std::vector<uint8_t> rows;
+    const uint64_t last = std::min<uint64_t>(lb, n > 0 ? n - 1 : 0);
+    entries.reserve(last);
+    rows.reserve(last);
+    for (uint64_t a = 0; a < last; ++a) {
+        entries.push_back({0u, sc.h_perm[a], (uint32_t)(a + 1), (uint32_t)(n - 1 - a)});
+        rows.push_back((uint8_t)systolic_rows(set->h_len[sc.h_perm[a]]));
+    }
+    if (n > 0) {
+        GBD_CUDA_TRY(cudaMalloc((void **)&sc.d_perm, n * sizeof(uint32_t)));
+        GBD_CUDA_TRY(cudaMemcpyAsync(sc.d_perm, sc.h_perm.data(), n * sizeof(uint32_t),
+                                     cudaMemcpyHostToDevice, st));
+    }
+    int rc = build_plan(entries, rows, sc.plan, true, st);
+    if (rc != GBD_OK) return rc;
+    GBD_CUDA_TRY(cudaStreamSynchronize(st));
+    sc.built = true;
+    return GBD_OK;
+}
+
+// Copies a host array into stream-ordered device memory freed by the caller.
+template <typename T>
+static int upload(const T *h, size_t count, T **d, cudaStream_t st)
+{
+    *d = nullptr;
+    if (count == 0) return GBD_OK;
+    GBD_CUDA_TRY(cudaMallocAsync((void **)d, count * sizeof(T), st));
+    GBD_CUDA_TRY(cudaMemcpyAsync(*d, h, count * sizeof(T), cudaMemcpyHostToDevice, st));
+    return GBD_OK;
+}
+
+// Triangle of one set through the systolic kernel (+ the general kernel for the pairs
+// of reads longer than the systolic query limit).
+static int all_pairs_systolic(gbd_ctx *ctx, gbd_set *set, uint16_t *d_tri, cudaStream_t st)
+{
+    int rc = build_tri_schedule(set, st);
+    if (rc != GBD_OK) return rc;
+    const TriSchedule &sc = set->sched;
+    SysJob job{};
+    job.Q = job.S = set->view();
+    job.sub_perm = sc.d_perm;
+    job.out = d_tri;
+    job.n = set->n;
+    job.mode = OUT_TRI;
+    job.conversion = ctx->params.conversion;
+    SysJob *d_job = nullptr;
+    if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
+    rc = run_systolic(d_job, sc.plan, ctx->sm_count, st);
+    cudaFreeAsync(d_job, st);
+    if (rc != GBD_OK) return rc;
+    if (sc.long_begin + 1 < set->n) {
+        GeneralJob gj{set->view(), set->view(), 0, set->n, 0, set->n, 0, OUT_TRI_PERM, d_tri};
+        gj.perm = sc.d_perm;
+        gj.p0 = sc.long_begin;
+        rc = run_general(gj, scoring_of(ctx), ctx->sm_count, st);
+    }
+    return rc;
+}
+
+}  // namespace gbd
+
+using namespace gbd;
+
+extern "C" {
+
+const char *gbd_last_error(void) { return t_last_error.c_str(); }
+
+void gbd_default_params(gbd_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->match = 1;
+    p->mismatch = -1;
+    p->gap = 1;
+    p->conversion = GBD_CONV_MAX;
+    p->kernel = GBD_KERNEL_AUTO;
+    p->hbm_budget = 0;
+    p->timeout_us = 0;
+}
+
+int gbd_create(gbd_ctx **out, int device, const gbd_params *p)
+{
+    if (!out) return fail(GBD_EINVAL, "gbd_create: out is NULL");
+    *out = nullptr;
+    gbd_params prm;
+    gbd_default_params(&prm);
+    if (p) prm = *p;
+    if (prm.gap < 0) return fail(GBD_EINVAL, "gbd_create: gap penalty must be >= 0");
+    if (prm.conversion < GBD_CONV_MAX || prm.conversion > GBD_CONV_SCORE)
+        return fail(GBD_EINVAL, "gbd_create: unknown conversion");
+    if (prm.kernel < GBD_KERNEL_AUTO || prm.kernel > GBD_KERNEL_SYSTOLIC)
+        return fail(GBD_EINVAL, "gbd_create: unknown kernel choice");
+    if (prm.kernel == GBD_KERNEL_SYSTOLIC && !default_scores(prm))
+        return fail(GBD_EINVAL, "gbd_create: the systolic kernel supports the default scores "
+                                "(+1/-1/gap 1) only");
+    int ndev = 0;
+    GBD_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(GBD_EINVAL, "gbd_create: no such device");
+    GBD_CUDA_TRY(cudaSetDevice(device));
+    gbd_ctx *ctx = new (std::nothrow) gbd_ctx();
+    if (!ctx) return fail(GBD_ENOMEM, "gbd_create: out of host memory");
+    ctx->device = device;
+    ctx->params = prm;
+    cudaError_t e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return cuda_fail(e, "cudaDeviceGetAttribute");
+    }
+    *out = ctx;
+    return GBD_OK;
+}
+
+void gbd_destroy(gbd_ctx *ctx) { delete ctx; }
+
+int gbd_load_reads(gbd_ctx *ctx, const uint8_t *seq, const uint64_t *offsets, uint64_t n,
+                   gbd_set **out, void *stream)
+{
+    if (!ctx || !out) return fail(GBD_EINVAL, "gbd_load_reads: NULL context or output");
+    *out = nullptr;
+    if (!offsets) return fail(GBD_EINVAL, "gbd_load_reads: offsets is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    GBD_CUDA_TRY(cudaSetDevice(ctx->device));
+    const bool dev_off = is_device_pointer(offsets);
+    std::vector<uint64_t> hoff(n + 1);
+    if (dev_off) {
+        GBD_CUDA_TRY(cudaMemcpyAsync(hoff.data(), offsets, (n + 1) * sizeof(uint64_t),
+                                     cudaMemcpyDeviceToHost, st));
+        GBD_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(hoff.data(), offsets, (n + 1) * sizeof(uint64_t));
+    }
+    gbd_set *set = new (std::nothrow) gbd_set();
+    if (!set) return fail(GBD_ENOMEM, "gbd_load_reads: out of host memory");
+    set->ctx = ctx;
+    set->device = ctx->device;
+    set->n = n;
+    set->h_len.resize(n);
+    uint32_t max_len = 0;
+    double sum = 0.0, sumsq = 0.0;
+    for (uint64_t r = 0; r < n; ++r) {
+        if (hoff[r + 1] < hoff[r]) {
+            delete set;
+            return fail(GBD_EINVAL, "gbd_load_reads: offsets decrease at read " + std::to_string(r));
+        }
+        const uint64_t L = hoff[r + 1] - hoff[r];
+        if (L > 65535) {
+            delete set;
+            return fail(GBD_EINVAL, "gbd_load_reads: read " + std::to_string(r) + " is longer than 65535");
+        }
+        set->h_len[r] = (uint16_t)L;
+        max_len = std::max<uint32_t>(max_len, (uint32_t)L);
+        sum += (double)L;
+        sumsq += (double)L * (double)L;
+    }
+    set->max_len = max_len;
+    set->stride = std::max<uint32_t>(1, (max_len + kBasesPerWord - 1) / kBasesPerWord);
+    set->pair_cells = (sum * sum - sumsq) * 0.5;
+    const uint64_t nbytes = hoff[n] - hoff[0];
+    if (nbytes > 0 && !seq) {
+        delete set;
+        return fail(GBD_EINVAL, "gbd_load_reads: seq is NULL");
+    }
+    if (n == 0) {
+        *out = set;
+        return GBD_OK;
+    }
+
+    cudaError_t e = cudaSuccess;
+    uint8_t *d_seq_tmp = nullptr;
+    uint64_t *d_off_tmp = nullptr;
+    unsigned long long *d_err = nullptr;
+    unsigned long long h_err = ~0ull;
+    const uint8_t *d_seq = seq;
+    const uint64_t *d_off = offsets;
+    auto cleanup = [&]() {
+        if (d_seq_tmp) cudaFreeAsync(d_seq_tmp, st);
+        if (d_off_tmp) cudaFreeAsync(d_off_tmp, st);
+        if (d_err) cudaFreeAsync(d_err, st);
+    };
+    do {
+        if ((e = cudaMalloc((void **)&set->d_words, n * set->stride * sizeof(uint32_t))) != cudaSuccess) break;
+        if ((e = cudaMalloc((void **)&set->d_len, n * sizeof(uint16_t))) != cudaSuccess) break;
+        if ((e = cudaMallocAsync((void **)&d_err, sizeof(unsigned long long), st)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(d_err, 0xff, sizeof(unsigned long long), st)) != cudaSuccess) break;
+        if (!dev_off) {
+            if ((e = cudaMallocAsync((void **)&d_off_tmp, (n + 1) * sizeof(uint64_t), st)) != cudaSuccess) break;
+            if ((e = cudaMemcpyAsync(d_off_tmp, hoff.data(), (n + 1) * sizeof(uint64_t),
+                                     cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+            d_off = d_off_tmp;
+        }
+        if (nbytes > 0 && !is_device_pointer(seq)) {
+            if ((e = cudaMallocAsync((void **)&d_seq_tmp, nbytes, st)) != cudaSuccess) break;
+            if ((e = cudaMemcpyAsync(d_seq_tmp, seq + hoff[0], nbytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+            // the kernel indexes seq with absolute offsets: shift the base pointer back
+            d_seq = d_seq_tmp - hoff[0];
+        }
+        if ((e = launch_pack(d_seq, d_off, n, set->stride, set->d_words, set->d_len, d_err, st)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(&h_err, d_err, sizeof h_err, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+        e = cudaStreamSynchronize(st);
+    } while (0);
+    cleanup();
+    if (e != cudaSuccess) {
+        gbd_free_set(set);
+        return cuda_fail(e, "gbd_load_reads");
+    }
+    if (h_err != ~0ull) {
+        gbd_free_set(set);
+        return fail(GBD_EINVAL, "gbd_load_reads: byte at position " + std::to_string(h_err) +
+                                    " is not one of A, C, G, T");
+    }
+    *out = set;
+    return GBD_OK;
+}
+
+void gbd_free_set(gbd_set *set)
+{
+    if (!set) return;
+    cudaSetDevice(set->device);
+    if (set->d_words) cudaFree(set->d_words);
+    if (set->d_len) cudaFree(set->d_len);
+    if (set->sched.d_perm) cudaFree(set->sched.d_perm);
+    gbd::free_plan(set->sched.plan, nullptr);
+    delete set;
+}
+
+uint64_t gbd_set_size(const gbd_set *set) { return set ? set->n : 0; }
+uint32_t gbd_set_max_len(const gbd_set *set) { return set ? set->max_len : 0; }
+double gbd_set_pair_cells(const gbd_set *set) { return set ? set->pair_cells : 0.0; }
+
+int gbd_all_pairs(gbd_ctx *ctx, const gbd_set *set, uint16_t *d_tri, uint64_t tri_len, void *stream)
+{
+    if (!ctx || !set) return fail(GBD_EINVAL, "gbd_all_pairs: NULL context or set");
+    const uint64_t n = set->n;
+    const uint64_t need = n < 2 ? 0 : n * (n - 1) / 2;
+    if (tri_len != need)
+        return fail(GBD_EINVAL, "gbd_all_pairs: tri_len is " + std::to_string(tri_len) +
+                                    ", expected n(n-1)/2 = " + std::to_string(need));
+    if (need == 0) return GBD_OK;
+    if (!d_tri) return fail(GBD_EINVAL, "gbd_all_pairs: d_tri is NULL");
+    GBD_CUDA_TRY(cudaSetDevice(ctx->device));
+    if (use_systolic(ctx))
+        return all_pairs_systolic(ctx, const_cast<gbd_set *>(set), d_tri, (cudaStream_t)stream);
+    GeneralJob job{set->view(), set->view(), 0, n, 0, n, 0, OUT_TRI, d_tri};
+    return run_general(job, scoring_of(ctx), ctx->sm_count, (cudaStream_t)stream);
+}
+
+int gbd_tile(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd_set *B,
+             uint64_t b0, uint64_t b1, uint16_t *d_out, uint64_t ld, void *stream)
+{
+    if (!ctx || !A || !B) return fail(GBD_EINVAL, "gbd_tile: NULL context or set");
+    if (a0 > a1 || a1 > A->n || b0 > b1 || b1 > B->n)
+        return fail(GBD_EINVAL, "gbd_tile: row or column range outside the sets");
+    if (ld < b1 - b0) return fail(GBD_EINVAL, "gbd_tile: ld is smaller than the column count");
+    if (a0 == a1 || b0 == b1) return GBD_OK;
+    if (!d_out) return fail(GBD_EINVAL, "gbd_tile: d_out is NULL");
+    GBD_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!use_systolic(ctx)) {
+        GeneralJob job{A->view(), B->view(), a0, a1, b0, b1, ld, OUT_RECT, d_out};
+        return run_general(job, scoring_of(ctx), ctx->sm_count, st);
+    }
+    std::vector<SysEntry> entries;
+    std::vector<uint8_t> rows;
+    std::vector<uint32_t> long_rows;
+    for (uint64_t r = a0; r < a1; ++r) {
+        if (A->h_len[r] <= kSystolicMaxQuery) {
+            entries.push_back({0u, (uint32_t)r, (uint32_t)b0, (uint32_t)(b1 - b0)});
+            rows.push_back((uint8_t)systolic_rows(A->h_len[r]));
+        } else {
+            long_rows.push_back((uint32_t)r);
+        }
+    }
+    int rc = GBD_OK;
+    if (!entries.empty()) {
+        SysJob job{};
+        job.Q = A->view();
+        job.S = B->view();
+        job.sub_perm = nullptr;
+        job.out = d_out;
+        job.ld = ld;
+        job.row0 = a0;
+        job.col0 = b0;
+        job.mode = OUT_RECT;
+        job.conversion = ctx->params.conversion;
+        SysJob *d_job = nullptr;
+        SysPlan plan;
+        if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
+        if ((rc = build_plan(entries, rows, plan, false, st)) != GBD_OK) return rc;
+        rc = run_systolic(d_job, plan, ctx->sm_count, st);
+        cudaFreeAsync(d_job, st);
+        free_plan(plan, st);
+        if (rc != GBD_OK) return rc;
+    }
+    if (!long_rows.empty()) {
+        uint32_t *d_rows = nullptr;
+        if ((rc = upload(long_rows.data(), long_rows.size(), &d_rows, st)) != GBD_OK) return rc;
+        GeneralJob gj{A->view(), B->view(), a0, a1, b0, b1, ld, OUT_RECT, d_out};
+        gj.rows = d_rows;
+        gj.nrows = long_rows.size();
+        rc = run_general(gj, scoring_of(ctx), ctx->sm_count, st);
+        cudaFreeAsync(d_rows, st);
+    }
+    return rc;
+}
+
+int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns, uint16_t *const *d_tris,
+              void *stream)
+{
+    if (!ctx || (ns > 0 && (!samples || !d_tris))) return fail(GBD_EINVAL, "gbd_batch: NULL argument");
+    for (uint64_t s = 0; s < ns; ++s) {
+        if (!samples[s]) return fail(GBD_EINVAL, "gbd_batch: NULL sample " + std::to_string(s));
+        if (samples[s]->n >= 2 && !d_tris[s]) return fail(GBD_EINVAL, "gbd_batch: NULL output " + std::to_string(s));
+    }
+    GBD_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!use_systolic(ctx)) {
+        for (uint64_t s = 0; s < ns; ++s) {
+            const uint64_t n = samples[s]->n;
+            if (n < 2) continue;
+            GeneralJob job{samples[s]->view(), samples[s]->view(), 0, n, 0, n, 0, OUT_TRI, d_tris[s]};
+            int rc = run_general(job, scoring_of(ctx), ctx->sm_count, st);
+            if (rc != GBD_OK) return rc;
+        }
+        return GBD_OK;
+    }
+    // one plan over every sample's entries, largest first; one launch per length bucket
+    std::vector<SysJob> jobs(ns);
+    std::vector<SysEntry> entries;
+    std::vector<uint8_t> rows;
+    for (uint64_t s = 0; s < ns; ++s) {
+        gbd_set *set = const_cast<gbd_set *>(samples[s]);
+        int rc = build_tri_schedule(set, st);
+        if (rc != GBD_OK) return rc;
+        SysJob &job = jobs[s];
+        job = SysJob{};
+        job.Q = job.S = set->view();
+        job.sub_perm = set->sched.d_perm;
+        job.out = d_tris[s];
+        job.n = set->n;
+        job.mode = OUT_TRI;
+        job.conversion = ctx->params.conversion;
+        const uint64_t n = set->n;
+        const uint64_t last = std::min<uint64_t>(set->sched.long_begin, n > 0 ? n - 1 : 0);
+        for (uint64_t a = 0; a < last; ++a) {
+            const uint32_t q = set->sched.h_perm[a];
+            entries.push_back({(uint32_t)s, q, (uint32_t)(a + 1), (uint32_t)(n - 1 - a)});
+            rows.push_back((uint8_t)systolic_rows(set->h_len[q]));
+        }
+    }
+    {
+        std::vector<size_t> order(entries.size());
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](size_t x, size_t y) { return entries[x].nsub > entries[y].nsub; });
+        std::vector<SysEntry> e2(entries.size());
+        std::vector<uint8_t> r2(entries.size());
+        for (size_t i = 0; i < order.size(); ++i) { e2[i] = entries[order[i]]; r2[i] = rows[order[i]]; }
+        entries.swap(e2);
+        rows.swap(r2);
+    }
+    int rc = GBD_OK;
+    if (!entries.empty()) {
+        SysJob *d_jobs = nullptr;
+        SysPlan plan;
+        if ((rc = upload(jobs.data(), jobs.size(), &d_jobs, st)) != GBD_OK) return rc;
+        if ((rc = build_plan(entries, rows, plan, false, st)) != GBD_OK) return rc;
+        rc = run_systolic(d_jobs, plan, ctx->sm_count, st);
+        cudaFreeAsync(d_jobs, st);
+        free_plan(plan, st);
+        if (rc != GBD_OK) return rc;
+    }
+    for (uint64_t s = 0; s < ns; ++s) {
+        const gbd_set *set = samples[s];
+        if (set->sched.long_begin + 1 < set->n) {
+            GeneralJob gj{set->view(), set->view(), 0, set->n, 0, set->n, 0, OUT_TRI_PERM, d_tris[s]};
+            gj.perm = set->sched.d_perm;
+            gj.p0 = set->sched.long_begin;
+            rc = run_general(gj, scoring_of(ctx), ctx->sm_count, st);
+            if (rc != GBD_OK) return rc;
+        }
+    }
+    return GBD_OK;
+}
+
+uint64_t gbd_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int gbd_probe_op_rate(int op, uint32_t iters, double *lane_ops_per_s, void *stream)
+{
+    int dev = 0, sms = 0;
+    GBD_CUDA_TRY(cudaGetDevice(&dev));
+    GBD_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return probe_op_rate(op, iters, lane_ops_per_s, sms, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gbd.h"
+
+namespace gbd {
+
+// ------------------------------------------------------------------ error plumbing
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define GBD_CUDA_TRY(call)                                   \
+    do {                                                     \
+        cudaError_t _e = (call);                             \
+        if (_e != cudaSuccess) return ::gbd::cuda_fail(_e, #call); \
+    } while (0)
+
+// Count of kernel launches made by the library (see gbd_kernel_launches).
+void note_launches(uint64_t k);
+
+// ------------------------------------------------------------------ packed read sets
+constexpr int kBasesPerWord = 16;
+
+struct DeviceReads {            // plain view passed to kernels
+    const uint32_t *words;      // n * stride 2-bit packed words
+    const uint16_t *len;        // n lengths
+    uint64_t n;
+    uint32_t stride;            // words per read
+};
+
+// Entries grouped by rows per lane, resident on the device.  Each non-empty bucket is
+// one launch of the kernel instantiated for its R.
+struct SysPlan {
+    struct Bucket {
+        int R = 0;
+        uint32_t nentries = 0, nunits = 0;
+        size_t entry_off = 0, prefix_off = 0;   // offsets into d_buf (bytes)
+    };
+    std::vector<Bucket> buckets;
+    void *d_buf = nullptr;
+    bool stream_ordered = false;   // d_buf from cudaMallocAsync (freed on a stream)
+    uint64_t units() const
+    {
+        uint64_t u = 0;
+        for (const auto &b : buckets) u += b.nunits;
+        return u;
+    }
+};
+
+// Device-resident schedule of a read set for the all-pairs triangle: the set's reads in
+// ascending length order, and one systolic entry per read short enough to be a systolic
+// query (query = sorted position a, subjects = sorted positions a+1 .. n-1).
+struct TriSchedule {
+    bool built = false;
+    std::vector<uint32_t> h_perm;
+    uint32_t *d_perm = nullptr;
+    SysPlan plan;                     // entries with job index 0
+    uint64_t long_begin = 0;          // sorted position of the first read longer than 512
+};
+
+}  // namespace gbd
+
+struct gbd_ctx {
+    int device = 0;
+    gbd_params params{};
+    int sm_count = 0;
+};
+
+struct gbd_set {
+    gbd_ctx *ctx = nullptr;
+    int device = 0;
+    uint64_t n = 0;
+    uint32_t stride = 0;        // words per read
+    uint32_t max_len = 0;
+    uint32_t *d_words = nullptr;
+    uint16_t *d_len = nullptr;
+    std::vector<uint16_t> h_len;
+    double pair_cells = 0.0;
+    gbd::TriSchedule sched;
+    gbd::DeviceReads view() const { return {d_words, d_len, n, stride}; }
+};
+
+namespace gbd {
+
+// ------------------------------------------------------------------ kernels (launchers)
+// K0: pack + validate.  seq/offsets are device pointers.  err receives the smallest
+// position (relative to offsets[0]) of an invalid byte, or UINT64_MAX.
+cudaError_t launch_pack(const uint8_t *seq, const uint64_t *offsets, uint64_t n, uint32_t stride,
+                        uint32_t *words, uint16_t *len, unsigned long long *err,
+                        cudaStream_t stream);
+
+// Output addressing of a block of pairs.
+//  OUT_TRI:      A == B, pairs i < j, out[k(i,j)] (row-major strict upper triangle)
+//  OUT_RECT:     out[(i-a0)*ld + (j-b0)]
+//  OUT_TRI_PERM: A == B, pairs (perm[p0+x], perm[p0+y]) for 0 <= x < y < n-p0, written at
+//                the triangle index of the two original indices
+enum OutMode : int { OUT_TRI = 0, OUT_RECT = 1, OUT_TRI_PERM = 2 };
+
+struct Scoring {
+    int match, mismatch, gap, conversion;
+};
+
+// General kernel: one pair per thread, int32 strip DP, boundary rows in scratch.
+struct GeneralJob {
+    DeviceReads A, B;
+    uint64_t a0, a1, b0, b1, ld;
+    int mode;
+    uint16_t *out;
+    const uint32_t *perm = nullptr;   // OUT_TRI_PERM: sorted order of the set
+    uint64_t p0 = 0;                  // OUT_TRI_PERM: first position of the sub-triangle
+    const uint32_t *rows = nullptr;   // OUT_RECT: optional explicit list of A rows
+    uint64_t nrows = 0;
+};
+int run_general(const GeneralJob &job, const Scoring &sc, int sm_count, cudaStream_t stream);
+
+// Instruction-rate probe.
+int probe_op_rate(int op, uint32_t iters, double *rate, int sm_count, cudaStream_t stream);
+
+}  // namespace gbd

@@ -1,0 +1,153 @@
+// General pair kernel: one read pair per thread, any lengths (<= 65535), any scores.
+//
+// Smith-Waterman local score (paper section 2.2) by the textbook recurrence
+//   H(i,j) = max(0, H(i-1,j-1) + s(a_i,b_j), H(i-1,j) - gap, H(i,j-1) - gap),
+// S = max H, converted to a distance in the epilogue.  The query read is swept in
+// strips of R rows held in registers; the strip's last row is handed to the next
+// strip through a per-thread boundary row in scratch memory, laid out column-major
+// over threads ([column][thread]) so a warp's loads and stores are coalesced.
+// This kernel is the path for reads longer than the systolic kernel's limit, for
+// non-default scores, and the simple baseline the fast kernel is checked against.
+#include <algorithm>
+
+#include "gbd_internal.cuh"
+
+namespace gbd {
+namespace {
+
+constexpr int kStrip = 8;
+
+__device__ __forceinline__ uint32_t base_at(const uint32_t *w, uint32_t k)
+{
+    return (__ldg(w + (k >> 4)) >> ((k & 15u) * 2u)) & 3u;
+}
+
+__device__ __forceinline__ uint64_t tri_row_start(uint64_t i, uint64_t n)
+{
+    return i * n - i * (i + 1) / 2;
+}
+
+// Row i of the strict upper triangle holding linear index k.
+__device__ __forceinline__ void tri_unindex(uint64_t k, uint64_t n, uint64_t &i, uint64_t &j)
+{
+    const double b = 2.0 * (double)n - 1.0;
+    double disc = b * b - 8.0 * (double)k;
+    disc = disc > 0.0 ? disc : 0.0;
+    int64_t r = (int64_t)((b - sqrt(disc)) * 0.5);
+    if (r < 0) r = 0;
+    if (r > (int64_t)n - 2) r = (int64_t)n - 2;
+    while (r + 1 <= (int64_t)n - 2 && tri_row_start((uint64_t)r + 1, n) <= k) ++r;
+    while (r > 0 && tri_row_start((uint64_t)r, n) > k) --r;
+    i = (uint64_t)r;
+    j = k - tri_row_start(i, n) + i + 1;
+}
+
+__device__ __forceinline__ uint16_t convert(int S, int la, int lb, int conversion)
+{
+    int d;
+    if (conversion == GBD_CONV_SCORE) d = S;
+    else if (conversion == GBD_CONV_MIN) d = min(la, lb) - S;
+    else d = max(la, lb) - S;
+    d = d < 0 ? 0 : (d > 65535 ? 65535 : d);
+    return (uint16_t)d;
+}
+
+__global__ void __launch_bounds__(128)
+sw_general_kernel(GeneralJob job, Scoring sc, int *__restrict__ scratch, uint64_t units)
+{
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+    int *bnd = scratch + tid;                       // bnd[j * nthr] = H(strip top - 1, j)
+    const uint64_t nb = job.b1 - job.b0;
+
+    for (uint64_t u = tid; u < units; u += nthr) {
+        uint64_t ia, jb, o;
+        if (job.mode == OUT_TRI) {
+            uint64_t ti, tj;
+            tri_unindex(u, job.A.n, ti, tj);
+            ia = ti; jb = tj; o = u;
+        } else if (job.mode == OUT_TRI_PERM) {
+            uint64_t x, y;
+            tri_unindex(u, job.A.n - job.p0, x, y);
+            const uint64_t pa = job.perm[job.p0 + x], pb = job.perm[job.p0 + y];
+            ia = pa < pb ? pa : pb;
+            jb = pa < pb ? pb : pa;
+            o = ia * job.A.n - ia * (ia + 1) / 2 + (jb - ia - 1);
+        } else {
+            const uint64_t r = u / nb;
+            ia = job.rows ? (uint64_t)job.rows[r] : job.a0 + r;
+            jb = job.b0 + (u - r * nb);
+            o = (ia - job.a0) * job.ld + (jb - job.b0);
+        }
+        const uint32_t *a = job.A.words + ia * job.A.stride;
+        const uint32_t *b = job.B.words + jb * job.B.stride;
+        const int la = job.A.len[ia];
+        const int lb = job.B.len[jb];
+        int best = 0;
+        for (int i0 = 0; i0 < la; i0 += kStrip) {
+            uint32_t ac[kStrip];
+#pragma unroll
+            for (int r = 0; r < kStrip; ++r) ac[r] = (i0 + r < la) ? base_at(a, i0 + r) : 4u;
+            int hl[kStrip];
+#pragma unroll
+            for (int r = 0; r < kStrip; ++r) hl[r] = 0;   // H(i, 0) = 0
+            int diag_top = 0;                                // H(i0, 0) = 0
+            for (int j = 1; j <= lb; ++j) {
+                const uint32_t c = base_at(b, j - 1);
+                int up = (i0 == 0) ? 0 : bnd[(uint64_t)j * nthr];   // H(i0, j)
+                int diag = diag_top;                                  // H(i0, j-1)
+                diag_top = up;
+#pragma unroll
+                for (int r = 0; r < kStrip; ++r) {
+                    const int s = (ac[r] == c) ? sc.match : sc.mismatch;
+                    int h = max(0, diag + s);
+                    h = max(h, up - sc.gap);
+                    h = max(h, hl[r] - sc.gap);
+                    diag = hl[r];
+                    hl[r] = h;
+                    up = h;
+                    if (i0 + r < la) best = max(best, h);
+                }
+                bnd[(uint64_t)j * nthr] = hl[kStrip - 1];
+            }
+        }
+        job.out[o] = convert(best, la, lb, sc.conversion);
+    }
+}
+
+}  // namespace
+
+int run_general(const GeneralJob &job, const Scoring &sc, int sm_count, cudaStream_t stream)
+{
+    uint64_t units;
+    if (job.mode == OUT_TRI) {
+        const uint64_t n = job.A.n;
+        units = n < 2 ? 0 : n * (n - 1) / 2;
+    } else if (job.mode == OUT_TRI_PERM) {
+        const uint64_t m = job.A.n - job.p0;
+        units = m < 2 ? 0 : m * (m - 1) / 2;
+    } else {
+        units = (job.rows ? job.nrows : (job.a1 - job.a0)) * (job.b1 - job.b0);
+    }
+    if (units == 0) return GBD_OK;
+    const int threads = 128;
+    // the boundary row needs (max column count + 1) ints per thread
+    const uint32_t maxlb = job.B.stride * kBasesPerWord;
+    uint64_t blocks = (uint64_t)std::max(sm_count, 1) * 8;
+    const uint64_t per_thread = (uint64_t)(maxlb + 1) * sizeof(int);
+    const uint64_t budget = 1ull << 30;   // at most 1 GiB of boundary rows
+    while (blocks > 1 && blocks * threads * per_thread > budget) blocks /= 2;
+    const uint64_t need_blocks = (units + threads - 1) / threads;
+    if (blocks > need_blocks) blocks = need_blocks;
+    int *scratch = nullptr;
+    GBD_CUDA_TRY(cudaMallocAsync((void **)&scratch, blocks * threads * per_thread, stream));
+    sw_general_kernel<<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units);
+    note_launches(1);
+    cudaError_t le = cudaGetLastError();
+    cudaError_t fe = cudaFreeAsync(scratch, stream);
+    if (le != cudaSuccess) return cuda_fail(le, "sw_general_kernel launch");
+    if (fe != cudaSuccess) return cuda_fail(fe, "cudaFreeAsync");
+    return GBD_OK;
+}
+
+}  // namespace gbd

@@ -1,0 +1,575 @@
+// Warp-systolic int16x2 Smith-Waterman kernel (the hot path).
+//
+// What it computes: the local alignment score S of section 2.2 (Smith-Waterman,
+// match +1, mismatch -1, linear gap 1) for one query read against a stream of
+// subject reads, then the distance d = max(la, lb) - S.
+//
+// Layout of the work (one warp = one work unit = one query vs many subjects):
+//  * Lane k owns query rows [kR, kR+R) (R = ceil(la/32) <= 16).  Subjects flow through
+//    the warp as a stream of columns; lane k runs 16 steps behind lane k-1, so the value
+//    of lane k-1's last row reaches lane k by a warp shuffle (plus a (16-R)-step delay
+//    line when R < 16).  The two 16-bit halves of every register carry two independent
+//    subject streams (int16x2 SIMD).
+//  * Within a lane, row r at local step u handles stream column u - r, so the R cells a
+//    lane updates per step lie on one anti-diagonal and are independent.
+//  * Scores are biased by the anti-diagonal: K(i,j) = H(i,j) + i + j + C.  The textbook
+//    recurrence H = max(0, H_d + s, H_u - 1, H_l - 1) becomes
+//        K = max(f, K_d + s + 2, K_u, K_l),    f = i + j + C  (the "zero" of the local
+//    alignment), i.e. one __viaddmax_s16x2 and one __vimax3_s16x2 per two cells.
+//  * s + 2 comes from a score profile in shared memory: for each query base q and
+//    stream column j, SP[q][j] = (s(q, b_lo[j]) + 2, s(q, b_hi[j]) + 2) as int16x2, or a
+//    large negative value where the column is padding.  The profile is a ring of 36
+//    chunks of 16 columns, refilled one chunk ahead by the whole warp; each lane reads
+//    it with 64-bit loads two steps at a time (a row's column advances by one per step).
+//  * Subjects start on 16-column chunk boundaries (a subject's 2-bit packed word = one
+//    chunk).  At a subject's first column, a row's left and diagonal inputs are reset to
+//    the floor (H(i,0) = 0) with one masked LOP3 per row per chunk.
+//  * S = max(K - f) is tracked per step (rows of the current and of the previous column
+//    chunk separately), folded per subject, and combined across lanes with a shuffle
+//    chain; lane 31 writes the converted distance.
+// Values are kept in [~1000, ~10700] by rebasing every 8192 steps, so int16 never
+// overflows and 0 acts as minus infinity.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "gbd_internal.cuh"
+#include "sw_systolic.cuh"
+
+namespace gbd {
+namespace {
+
+constexpr int LANES = 32;
+constexpr int CH = 16;                       // steps per chunk == lane skew
+constexpr int RING_CHUNKS = 36;              // >= 34 chunks live at once
+constexpr int RING = RING_CHUNKS * CH;       // 576 columns
+constexpr int SLOTS = RING + 3 * CH;         // ring index in [-16, RING + 32)
+// +2 pad words per 16 columns; arrays start on 32-word (128-byte) boundaries so every
+// lane's bank position depends on its column alone
+constexpr int PWORDS = (SLOTS + 2 * (SLOTS / 16) + 31) & ~31;
+constexpr int NARR = 5;                      // profiles for A, C, G, T, and padding rows
+constexpr int TABLE_WORDS = RING_CHUNKS * 8; // per chunk: 8 words of stream metadata
+constexpr int TABLE_OFF = (NARR * PWORDS + 3) & ~3;   // 16-byte aligned table
+constexpr int WARP_WORDS = TABLE_OFF + TABLE_WORDS;
+constexpr int WARPS_PER_BLOCK = 2;
+constexpr uint32_t NEG2 = 0xC000C000u;       // (-16384, -16384)
+constexpr int C0 = 1536;                     // floor offset: f >= ~1000 for every lane
+constexpr uint32_t ONE2 = 0x00010001u;
+constexpr int REBASE_CHUNKS = 512;           // 8192 steps
+constexpr uint32_t REBASE2 = 0x20002000u;    // 8192 in both halves
+static_assert(PWORDS % 32 == 0, "profile arrays are 128-byte aligned");
+static_assert((REBASE_CHUNKS & (REBASE_CHUNKS - 1)) == 0, "rebase period is a power of two");
+static_assert(TABLE_OFF % 4 == 0 && WARP_WORDS % 4 == 0, "table and warp regions are 16-byte aligned");
+
+// padded word index of ring slot rho (rho in [-16, RING + 32))
+__host__ __device__ constexpr int pslot(int rho) { return (rho + 16) + 2 * ((rho + 16) >> 4); }
+// offset (in words) of relative column e in [-16, 17] from a chunk base P0
+__host__ __device__ constexpr int poff(int e) { return e < 0 ? e - 2 : (e < 16 ? e : e + 2); }
+__device__ __forceinline__ int chunk_P0(int c)
+{
+    int m = c % RING_CHUNKS;
+    if (m < 0) m += RING_CHUNKS;
+    return 18 * m + 18;       // == pslot(16 * m)
+}
+
+__device__ __forceinline__ uint32_t vmax3(uint32_t a, uint32_t b, uint32_t c) { return __vimax3_s16x2(a, b, c); }
+__device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b) { return __vmaxs2(a, b); }
+__device__ __forceinline__ uint32_t vaddmax(uint32_t a, uint32_t b, uint32_t c) { return __viaddmax_s16x2(a, b, c); }
+// (v, v) packed as int16x2 for a small signed v; building it as v * 0x00010001 would let
+// a negative low half borrow from the high half.
+__host__ __device__ constexpr uint32_t pack2(int v) { return ((uint32_t)v & 0xffffu) * 0x00010001u; }
+
+__device__ __forceinline__ uint32_t lop_sel(uint32_t keep, uint32_t repl, uint32_t mask)
+{
+    return (keep & ~mask) | (repl & mask);
+}
+
+__device__ __forceinline__ uint16_t convert_d(int S, int la, int lb, int conversion)
+{
+    int d;
+    if (conversion == GBD_CONV_SCORE) d = S;
+    else if (conversion == GBD_CONV_MIN) d = min(la, lb) - S;
+    else d = max(la, lb) - S;
+    d = d < 0 ? 0 : (d > 65535 ? 65535 : d);
+    return (uint16_t)d;
+}
+
+// One warp's work: a piece of an entry.
+struct SysUnit {
+    uint32_t job, q, sub_begin, nsub;
+};
+
+// Warp-uniform cursor over one half's subject stream.
+struct Cursor {
+    uint32_t pos, cnt, ck, nck, orig, len, next_orig, next_len;
+};
+
+__device__ __forceinline__ void subject_at(const SysJob &J, uint32_t list_index, uint32_t &orig,
+                                           uint32_t &len)
+{
+    orig = J.sub_perm ? __ldg(J.sub_perm + list_index) : list_index;
+    len = __ldg(J.S.len + orig);
+}
+
+__device__ __forceinline__ uint32_t nchunks(uint32_t len) { return len == 0 ? 1u : (len + 15u) >> 4; }
+
+__device__ __forceinline__ void cursor_init(Cursor &cu, const SysJob &J, const SysUnit &u, int h)
+{
+    cu.cnt = (u.nsub + 1 - h) >> 1;            // half h takes list positions h, h+2, ...
+    cu.pos = 0;
+    cu.ck = 0;
+    if (cu.cnt > 0) {
+        subject_at(J, u.sub_begin + h, cu.orig, cu.len);
+        cu.nck = nchunks(cu.len);
+    } else {
+        cu.orig = 0; cu.len = 0; cu.nck = 0xffffffffu;
+    }
+    if (cu.cnt > 1) subject_at(J, u.sub_begin + h + 2, cu.next_orig, cu.next_len);
+    else { cu.next_orig = 0; cu.next_len = 0; }
+}
+
+__device__ __forceinline__ void cursor_advance(Cursor &cu, const SysJob &J, const SysUnit &u, int h)
+{
+    if (cu.pos >= cu.cnt) return;
+    if (++cu.ck < cu.nck) return;
+    cu.ck = 0;
+    ++cu.pos;
+    cu.orig = cu.next_orig;
+    cu.len = cu.next_len;
+    if (cu.pos < cu.cnt) {
+        cu.nck = nchunks(cu.len);
+        if (cu.pos + 1 < cu.cnt) subject_at(J, u.sub_begin + h + 2 * (cu.pos + 1), cu.next_orig, cu.next_len);
+    } else {
+        cu.nck = 0xffffffffu;
+    }
+}
+
+// Stream metadata + packed word of the chunk a cursor points at.
+struct ChunkInfo {
+    uint32_t word;      // 16 bases, 2 bits each
+    uint32_t nvalid;    // valid columns in this chunk (0 = padding chunk)
+    uint32_t first, last;
+    uint32_t orig, len;
+};
+
+__device__ __forceinline__ void cursor_chunk(const Cursor &cu, const SysJob &J, ChunkInfo &ci)
+{
+    const bool valid = cu.pos < cu.cnt;
+    ci.first = valid && cu.ck == 0;
+    ci.last = valid && cu.ck + 1 == cu.nck;
+    ci.orig = cu.orig;
+    ci.len = cu.len;
+    if (valid) {
+        const uint32_t base = cu.ck * 16u;
+        ci.nvalid = cu.len > base ? min(16u, cu.len - base) : 0u;
+        ci.word = __ldg(J.S.words + (uint64_t)cu.orig * J.S.stride + cu.ck);
+    } else {
+        ci.nvalid = 0;
+        ci.word = 0;
+    }
+}
+
+// Write chunk X of the two half streams into the warp's profile ring and table.
+// m = X mod RING_CHUNKS, the ring slot of stream chunk X.
+__device__ __forceinline__ void fill_chunk(uint32_t *ws, int lane, int m, const ChunkInfo &lo,
+                                           const ChunkInfo &hi)
+{
+    const int x = lane & 15;
+    const int qa = (lane >> 4) * 2;
+    const uint32_t blo = (lo.word >> (2 * x)) & 3u, bhi = (hi.word >> (2 * x)) & 3u;
+    const bool vlo = (uint32_t)x < lo.nvalid, vhi = (uint32_t)x < hi.nvalid;
+    const int rho = 16 * m + x;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const uint32_t q = (uint32_t)(qa + t);
+        const uint32_t slo = vlo ? (blo == q ? 3u : 1u) : 0xC000u;
+        const uint32_t shi = vhi ? (bhi == q ? 3u : 1u) : 0xC000u;
+        const uint32_t v = slo | (shi << 16);
+        uint32_t *arr = ws + q * PWORDS;
+        arr[pslot(rho)] = v;
+        if (rho < 32) arr[pslot(rho + RING)] = v;
+        if (rho >= RING - 16) arr[pslot(rho - RING)] = v;
+    }
+    if (lane == 0) {
+        uint32_t *e = ws + TABLE_OFF + 8 * m;
+        e[0] = (lo.first ? 0x0000ffffu : 0u) | (hi.first ? 0xffff0000u : 0u);
+        e[1] = (lo.last ? 0x0000ffffu : 0u) | (hi.last ? 0xffff0000u : 0u);
+        e[2] = lo.len | (hi.len << 16);
+        e[3] = 0;
+        e[4] = lo.orig;
+        e[5] = hi.orig;
+    }
+}
+
+__device__ __forceinline__ uint2 lds64(const uint32_t *ws_words, uint32_t byte_off)
+{
+    return *reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(ws_words) + byte_off);
+}
+
+template <int R>
+__device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint32_t *ws, int lane,
+                                      uint32_t *err)
+{
+    constexpr int D = CH - R;                 // delay steps between lanes
+    const int la = J.Q.len[u.q];
+    const uint32_t *qwords = J.Q.words + (uint64_t)u.q * J.Q.stride;
+
+    // ---- stream cursors (warp-uniform) and the first two chunks of the ring
+    Cursor cur_lo, cur_hi;
+    cursor_init(cur_lo, J, u, 0);
+    cursor_init(cur_hi, J, u, 1);
+    ChunkInfo ci_lo, ci_hi;
+    cursor_chunk(cur_lo, J, ci_lo);
+    cursor_chunk(cur_hi, J, ci_hi);
+    fill_chunk(ws, lane, 0, ci_lo, ci_hi);        // ring slot 0
+    cursor_advance(cur_lo, J, u, 0);
+    cursor_advance(cur_hi, J, u, 1);
+    cursor_chunk(cur_lo, J, ci_lo);           // pending: chunk 1
+    cursor_chunk(cur_hi, J, ci_hi);
+    int C = -1;                                // stream length in chunks, once known
+    if (cur_lo.pos >= cur_lo.cnt && cur_hi.pos >= cur_hi.cnt) C = 1;
+    __syncwarp();
+
+    // ---- per-row profile addresses
+    uint32_t addr[R];
+    {
+        const int P0 = chunk_P0(-lane);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int pos = lane * R + r;
+            uint32_t code = 4;
+            if (pos < la) code = (__ldg(qwords + (pos >> 4)) >> (2 * (pos & 15))) & 3u;
+            addr[r] = (code * PWORDS + P0) * 4u;
+        }
+    }
+
+    // ---- registers of the systolic state
+    const int fk0 = 1 + C0 - lane * D;         // floor of this lane at global step 0
+    uint32_t f_prev2 = (uint32_t)(fk0 - 2) * ONE2;
+    uint32_t f_prev = (uint32_t)(fk0 - 1) * ONE2;
+    uint32_t V0[R], V1[R];                     // V0: even local steps, V1: odd
+#pragma unroll
+    for (int r = 0; r < R; ++r) { V1[r] = f_prev; V0[r] = f_prev2; }
+    uint32_t fifo[D > 0 ? D : 1];
+#pragma unroll
+    for (int i = 0; i < (D > 0 ? D : 1); ++i) fifo[i] = f_prev;
+    uint32_t sendv = f_prev;                   // row R-1 value offered to the next lane
+    uint32_t up0_prev = f_prev2;               // row 0's diagonal input
+    uint32_t curRel = 0, prevRel = 0, acc = 0, emit = 0;
+    uint32_t Mlast_prev = 0;                   // "ends a subject" masks of chunk c-1
+    uint32_t lens_prev = 0, orig_lo_prev = 0, orig_hi_prev = 0;
+    uint2 sp[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e0 = (r & 1) ? -r - 1 : -r;
+        sp[r] = lds64(ws, addr[r] + 4 * poff(e0));
+    }
+    // ring slots (mod RING_CHUNKS) of the chunk being filled and of this lane's chunk
+    int m_fill = 1;
+    int m_c = (RING_CHUNKS - lane % RING_CHUNKS) % RING_CHUNKS;
+
+    for (int g = 0; C < 0 || g < C + LANES; ++g) {
+        // ---- refill: pending chunk g+1 into the ring, then read ahead chunk g+2
+        fill_chunk(ws, lane, m_fill, ci_lo, ci_hi);
+        m_fill = (m_fill == RING_CHUNKS - 1) ? 0 : m_fill + 1;
+        cursor_advance(cur_lo, J, u, 0);
+        cursor_advance(cur_hi, J, u, 1);
+        cursor_chunk(cur_lo, J, ci_lo);
+        cursor_chunk(cur_hi, J, ci_hi);
+        if (C < 0 && cur_lo.pos >= cur_lo.cnt && cur_hi.pos >= cur_hi.cnt) C = g + 2;
+        __syncwarp();
+
+        // ---- rebase every REBASE_CHUNKS chunks (all lanes at the same global step)
+        if (g > 0 && (g & (REBASE_CHUNKS - 1)) == 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) { V0[r] -= REBASE2; V1[r] -= REBASE2; }
+#pragma unroll
+            for (int i = 0; i < (D > 0 ? D : 1); ++i) fifo[i] -= REBASE2;
+            sendv -= REBASE2; up0_prev -= REBASE2; f_prev -= REBASE2; f_prev2 -= REBASE2;
+            prevRel -= REBASE2;               // curRel is 0 (minus infinity) here
+        }
+
+        // ---- this lane's chunk c: stream metadata
+        const int c = g - lane;
+        uint32_t Mfirst = 0, Mend;                 // Mend: chunk c-1 ended a subject
+        uint32_t lens_c = 0, olo_c = 0, ohi_c = 0, Mlast_c = 0;
+        if (c >= 0) {
+            const uint32_t *e = ws + TABLE_OFF + 8 * m_c;
+            const uint4 ev = *reinterpret_cast<const uint4 *>(e);
+            Mfirst = ev.x; Mlast_c = ev.y; lens_c = ev.z;
+            olo_c = e[4]; ohi_c = e[5];
+        }
+        Mend = (c >= 1) ? Mlast_prev : 0xffffffffu;   // c <= 0: discard what came before
+        const uint32_t fbase = f_prev + ONE2;         // floor at step 0 of this chunk
+
+        // ---- 16 steps
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            uint32_t *cur = (q & 1) ? V0 : V1;        // V(u-1)
+            uint32_t *nxt = (q & 1) ? V1 : V0;        // V(u-2) in, V(u) out
+            const uint32_t f = f_prev + ONE2;
+            const uint32_t got = __shfl_up_sync(0xffffffffu, sendv, 1);
+            uint32_t up0;
+            if constexpr (D > 0) {
+                up0 = fifo[0];
+#pragma unroll
+                for (int i = 0; i + 1 < D; ++i) fifo[i] = fifo[i + 1];
+                fifo[D - 1] = got;
+            } else {
+                up0 = got;
+            }
+            if (lane == 0) up0 = f_prev;              // top boundary: H(0, j) = 0
+            uint32_t diag0 = up0_prev;
+#pragma unroll
+            for (int r = R - 1; r >= 0; --r) {
+                if (r == q) {
+                    // row q reaches a subject's first column: its left input (and, for
+                    // row 0, its diagonal) become the floor of column 0.  Rows below
+                    // already read the old value as their "up" input this step.
+                    cur[r] = lop_sel(cur[r], f_prev, Mfirst);
+                    if (r == 0) diag0 = lop_sel(diag0, f_prev2, Mfirst);
+                }
+                const uint32_t up = r ? cur[r - 1] : up0;
+                const uint32_t dg = r ? nxt[r - 1] : diag0;
+                const uint32_t s2 = (((q - r) & 1) == 0) ? sp[r].x : sp[r].y;
+                const uint32_t E = vaddmax(dg, s2, f);
+                nxt[r] = vmax3(up, cur[r], E);
+                if (((q - r) & 1) != 0) sp[r] = lds64(ws, addr[r] + 4 * poff(q + 1 - r));
+            }
+            sendv = nxt[R - 1];
+            up0_prev = up0;
+            // best: rows <= q are in column chunk c, rows > q in chunk c-1
+            {
+                const int nN = (q < R - 1 ? q : R - 1) + 1;
+                uint32_t mN = nxt[0];
+#pragma unroll
+                for (int r = 1; r < R; r += 2) {
+                    if (r < nN) {
+                        if (r + 1 < nN) mN = vmax3(mN, nxt[r], nxt[r + 1]);
+                        else mN = vmax2(mN, nxt[r]);
+                    }
+                }
+                curRel = vaddmax(mN, pack2(-q), curRel);
+                if (nN < R) {
+                    uint32_t mO = nxt[nN];
+#pragma unroll
+                    for (int r = 1; r < R; r += 2) {
+                        const int a = nN + r, b = nN + r + 1;
+                        if (a < R) {
+                            if (b < R) mO = vmax3(mO, nxt[a], nxt[b]);
+                            else mO = vmax2(mO, nxt[a]);
+                        }
+                    }
+                    prevRel = vaddmax(mO, pack2(-q), prevRel);
+                }
+            }
+            f_prev2 = f_prev;
+            f_prev = f;
+        }
+
+        // ---- chunk end: fold chunk c-1, pass totals down the lanes, write results
+        {
+            uint32_t recv = __shfl_up_sync(0xffffffffu, emit, 1);
+            if (lane == 0) recv = 0;
+            const uint32_t negfb = pack2(-(int)(fbase & 0xffffu));
+            const uint32_t a = vaddmax(prevRel, negfb, acc);       // max(acc, prev - fbase)
+            const uint32_t total = vmax2(a, recv);
+            emit = lop_sel(emit, total, Mend);
+            acc = a & ~Mend;
+            prevRel = curRel + 16u * ONE2;
+            curRel = 0;
+            if (lane == LANES - 1 && c >= 1 && Mend != 0) {
+                const int conv = J.conversion;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if ((Mend >> (16 * h)) & 1u) {
+                        const int S = (int)(int16_t)(total >> (16 * h));
+                        const uint32_t so = h ? orig_hi_prev : orig_lo_prev;
+                        const int lb = (int)((lens_prev >> (16 * h)) & 0xffffu);
+                        uint64_t idx;
+                        if (J.mode == OUT_TRI) {
+                            const uint64_t i = min((uint64_t)u.q, (uint64_t)so);
+                            const uint64_t j = max((uint64_t)u.q, (uint64_t)so);
+                            idx = i * J.n - i * (i + 1) / 2 + (j - i - 1);
+                        } else {
+                            idx = ((uint64_t)u.q - J.row0) * J.ld + ((uint64_t)so - J.col0);
+                        }
+                        J.out[idx] = convert_d(S, la, lb, conv);
+                    }
+                }
+            }
+            Mlast_prev = (c >= 0) ? Mlast_c : 0u;
+            lens_prev = lens_c;
+            orig_lo_prev = olo_c;
+            orig_hi_prev = ohi_c;
+        }
+        // ---- advance the profile addresses by one chunk
+        {
+            const bool wrap = (m_c == RING_CHUNKS - 1);
+            const uint32_t d = wrap ? (uint32_t)(4 * 18 * (1 - RING_CHUNKS)) : (uint32_t)(4 * 18);
+#pragma unroll
+            for (int r = 0; r < R; ++r) addr[r] += d;
+            m_c = wrap ? 0 : m_c + 1;
+        }
+        (void)err;
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 7)
+sw_systolic_kernel(const SysJob *__restrict__ jobs, const SysEntry *__restrict__ entries,
+                   const uint32_t *__restrict__ prefix, uint32_t nentries, uint32_t nunits,
+                   uint32_t *counter, uint32_t *err)
+{
+    extern __shared__ uint32_t smem[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    uint32_t *ws = smem + warp * WARP_WORDS;
+    for (int i = lane; i < WARP_WORDS; i += 32) ws[i] = NEG2;
+    __syncwarp();
+    for (;;) {
+        uint32_t ui = 0;
+        if (lane == 0) ui = atomicAdd(counter, 1u);
+        ui = __shfl_sync(0xffffffffu, ui, 0);
+        if (ui >= nunits) break;
+        // entry e with prefix[e] <= ui < prefix[e+1]
+        uint32_t lo = 0, hi = nentries;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(prefix + mid) <= ui) lo = mid; else hi = mid;
+        }
+        const SysEntry en = entries[lo];
+        const uint32_t piece = ui - __ldg(prefix + lo);
+        SysUnit u;
+        u.job = en.job;
+        u.q = en.q;
+        u.sub_begin = en.sub_begin + piece * kSystolicPiece;
+        u.nsub = min(kSystolicPiece, en.nsub - piece * kSystolicPiece);
+        run_unit<R>(jobs[u.job], u, ws, lane, err);
+        __syncwarp();
+    }
+}
+
+template <int R>
+int launch_bucket(const SysJob *d_jobs, const SysEntry *entries, const uint32_t *prefix,
+                  uint32_t nentries, uint32_t nunits, uint32_t *counter, uint32_t *err,
+                  int sm_count, cudaStream_t stream)
+{
+    const size_t smem = systolic_smem_bytes();
+    static bool attr_set = false;
+    if (!attr_set) {
+        GBD_CUDA_TRY(cudaFuncSetAttribute(sw_systolic_kernel<R>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    int per_sm = 0;
+    GBD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sw_systolic_kernel<R>,
+                                                                WARPS_PER_BLOCK * 32, smem));
+    if (per_sm < 1) return fail(GBD_ECUDA, "systolic kernel does not fit on an SM");
+    uint64_t blocks = (uint64_t)sm_count * per_sm;
+    const uint64_t need = (nunits + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+    if (blocks > need) blocks = need;
+    sw_systolic_kernel<R><<<(unsigned)blocks, WARPS_PER_BLOCK * 32, smem, stream>>>(
+        d_jobs, entries, prefix, nentries, nunits, counter, err);
+    note_launches(1);
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) return cuda_fail(le, "sw_systolic_kernel launch");
+    return GBD_OK;
+}
+
+}  // namespace
+
+size_t systolic_smem_bytes() { return (size_t)WARPS_PER_BLOCK * WARP_WORDS * sizeof(uint32_t); }
+
+int build_plan(const std::vector<SysEntry> &entries, const std::vector<uint8_t> &rows,
+               SysPlan &plan, bool persistent, cudaStream_t stream)
+{
+    plan = SysPlan{};
+    std::vector<std::vector<SysEntry>> by_r(17);
+    for (size_t i = 0; i < entries.size(); ++i) {
+        if (entries[i].nsub == 0) continue;
+        const int R = rows[i];
+        if (R < 1 || R > 16) return fail(GBD_EINVAL, "internal: systolic query longer than 512");
+        by_r[R].push_back(entries[i]);
+    }
+    // layout: for each bucket, entries (16 B each) then prefix (nentries + 1 words)
+    size_t bytes = 0;
+    std::vector<std::vector<uint32_t>> prefixes(17);
+    for (int R = 16; R >= 1; --R) {          // launch order: widest rows first
+        if (by_r[R].empty()) continue;
+        SysPlan::Bucket b;
+        b.R = R;
+        b.nentries = (uint32_t)by_r[R].size();
+        std::vector<uint32_t> &pf = prefixes[R];
+        pf.resize(b.nentries + 1);
+        uint64_t acc = 0;
+        for (uint32_t e = 0; e < b.nentries; ++e) {
+            pf[e] = (uint32_t)acc;
+            acc += (by_r[R][e].nsub + kSystolicPiece - 1) / kSystolicPiece;
+        }
+        if (acc >= 0xffffffffull) return fail(GBD_EINVAL, "too many work units for one launch");
+        pf[b.nentries] = (uint32_t)acc;
+        b.nunits = (uint32_t)acc;
+        b.entry_off = bytes;
+        bytes += b.nentries * sizeof(SysEntry);
+        b.prefix_off = bytes;
+        bytes += (b.nentries + 1) * sizeof(uint32_t);
+        bytes = (bytes + 15) & ~size_t(15);
+        plan.buckets.push_back(b);
+    }
+    if (bytes == 0) return GBD_OK;
+    std::vector<uint8_t> host(bytes);
+    for (const auto &b : plan.buckets) {
+        std::memcpy(host.data() + b.entry_off, by_r[b.R].data(), b.nentries * sizeof(SysEntry));
+        std::memcpy(host.data() + b.prefix_off, prefixes[b.R].data(), (b.nentries + 1) * sizeof(uint32_t));
+    }
+    plan.stream_ordered = !persistent;
+    if (persistent) {
+        GBD_CUDA_TRY(cudaMalloc(&plan.d_buf, bytes));
+    } else {
+        GBD_CUDA_TRY(cudaMallocAsync(&plan.d_buf, bytes, stream));
+    }
+    GBD_CUDA_TRY(cudaMemcpyAsync(plan.d_buf, host.data(), bytes, cudaMemcpyHostToDevice, stream));
+    if (persistent) GBD_CUDA_TRY(cudaStreamSynchronize(stream));
+    return GBD_OK;
+}
+
+void free_plan(SysPlan &plan, cudaStream_t stream)
+{
+    if (plan.d_buf) {
+        if (plan.stream_ordered) cudaFreeAsync(plan.d_buf, stream);
+        else cudaFree(plan.d_buf);
+    }
+    plan = SysPlan{};
+}
+
+int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaStream_t stream)
+{
+    if (plan.buckets.empty()) return GBD_OK;
+    const size_t nb = plan.buckets.size();
+    uint32_t *scratch = nullptr;                  // per bucket: work counter, error flags
+    GBD_CUDA_TRY(cudaMallocAsync((void **)&scratch, 2 * nb * sizeof(uint32_t), stream));
+    GBD_CUDA_TRY(cudaMemsetAsync(scratch, 0, 2 * nb * sizeof(uint32_t), stream));
+    int rc = GBD_OK;
+    for (size_t i = 0; i < nb && rc == GBD_OK; ++i) {
+        const SysPlan::Bucket &b = plan.buckets[i];
+        const char *base = static_cast<const char *>(plan.d_buf);
+        const SysEntry *en = reinterpret_cast<const SysEntry *>(base + b.entry_off);
+        const uint32_t *pf = reinterpret_cast<const uint32_t *>(base + b.prefix_off);
+        uint32_t *ctr = scratch + 2 * i, *err = scratch + 2 * i + 1;
+        switch (b.R) {
+#define GBD_CASE(RR) case RR: rc = launch_bucket<RR>(d_jobs, en, pf, b.nentries, b.nunits, ctr, err, sm_count, stream); break;
+            GBD_CASE(1) GBD_CASE(2) GBD_CASE(3) GBD_CASE(4) GBD_CASE(5) GBD_CASE(6) GBD_CASE(7)
+            GBD_CASE(8) GBD_CASE(9) GBD_CASE(10) GBD_CASE(11) GBD_CASE(12) GBD_CASE(13)
+            GBD_CASE(14) GBD_CASE(15) GBD_CASE(16)
+#undef GBD_CASE
+            default: rc = fail(GBD_EINVAL, "internal: bad rows per lane");
+        }
+    }
+    cudaError_t fe = cudaFreeAsync(scratch, stream);
+    if (rc != GBD_OK) return rc;
+    if (fe != cudaSuccess) return cuda_fail(fe, "cudaFreeAsync");
+    return GBD_OK;
+}
+
+}  // namespace gbd

@@ -1,0 +1,43 @@
+// Host/device interface of the warp-systolic kernel.
+#pragma once
+
+#include "gbd_internal.cuh"
+
+namespace gbd {
+
+// Reads up to this length can be the query (row) read of a systolic work unit.
+constexpr int kSystolicMaxQuery = 512;
+// Work units cover at most this many subjects (bounds the tail of every launch).
+constexpr uint32_t kSystolicPiece = 1024;
+
+// One output problem: queries of Q against subjects of S.
+struct SysJob {
+    DeviceReads Q, S;
+    const uint32_t *sub_perm;   // subject list (original indices in S); NULL = identity
+    uint16_t *out;
+    uint64_t n;                 // OUT_TRI: reads in the set
+    uint64_t ld, row0, col0;    // OUT_RECT: out[(q-row0)*ld + (s-col0)]
+    int mode;                   // OUT_TRI or OUT_RECT
+    int conversion;
+};
+
+// One query (original index q in Q, length <= 512) against the subjects at list
+// positions [sub_begin, sub_begin + nsub); split into units of kSystolicPiece subjects.
+struct SysEntry {
+    uint32_t job, q, sub_begin, nsub;
+};
+
+// Rows per lane of a query of length la (1..16 for la <= 512).
+inline int systolic_rows(int la) { return la <= 32 ? 1 : (la + 31) / 32; }
+
+// Groups entries by R (rows[i] = R of entries[i]) and uploads them.  Entries keep their
+// order inside a bucket (callers put the largest first).  persistent: cudaMalloc (kept
+// with a read set) instead of stream-ordered memory.
+int build_plan(const std::vector<SysEntry> &entries, const std::vector<uint8_t> &rows,
+               SysPlan &plan, bool persistent, cudaStream_t stream);
+void free_plan(SysPlan &plan, cudaStream_t stream);
+
+int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaStream_t stream);
+size_t systolic_smem_bytes();
+
+}  // namespace gbd

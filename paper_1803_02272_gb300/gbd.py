@@ -1,0 +1,302 @@
+"""Thin Python binding of the gbd C ABI (include/gbd.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no compute:
+all of the path (packing, scheduling, DP, conversion, stores) runs in libgbd.so's CUDA
+kernels.  PyTorch is used for device memory and streams: output buffers are torch
+tensors and `stream` defaults to torch's current CUDA stream.
+
+Importing this module loads libgbd.so and raises if it has not been built -- there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libgbd.so")
+
+GBD_OK, GBD_EINVAL, GBD_ENOMEM, GBD_EBUDGET, GBD_ETIMEDOUT, GBD_ECUDA, GBD_ENOTFOUND = range(7)
+GBD_CONV_MAX, GBD_CONV_MIN, GBD_CONV_SCORE = 0, 1, 2
+GBD_KERNEL_AUTO, GBD_KERNEL_GENERAL, GBD_KERNEL_SYSTOLIC = 0, 1, 2
+PROBE_OPS = ["VIMAX3_S16X2_RELU", "VIADDMAX_S16X2", "VIADDMAX_S16X2_RELU", "VIMAX_S16X2_RELU",
+             "VMAXS2", "PRMT", "IADD3", "LOP3", "IMAX", "HMAX2", "HADD2", "CELL_MIX",
+             "VIMAX3_S16X2", "FMAX", "FMAX3", "FADD", "MIX_DPX_HMAX2", "MIX_DPX_FMAX3",
+             "MIX_DPX_IADD3"]
+
+# every symbol include/gbd.h declares (checked by the tests)
+EXPORTS = [
+    "gbd_default_params", "gbd_create", "gbd_destroy", "gbd_load_reads", "gbd_free_set",
+    "gbd_set_size", "gbd_set_max_len", "gbd_set_pair_cells", "gbd_all_pairs", "gbd_tile",
+    "gbd_batch", "gbd_server_create", "gbd_server_submit", "gbd_server_poll",
+    "gbd_server_wait", "gbd_server_destroy", "gbd_last_error", "gbd_probe_op_rate",
+    "gbd_kernel_launches",
+]
+
+
+class GbdParams(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_int16), ("mismatch", ctypes.c_int16),
+                ("gap", ctypes.c_int16), ("conversion", ctypes.c_int16),
+                ("kernel", ctypes.c_int32), ("hbm_budget", ctypes.c_uint64),
+                ("timeout_us", ctypes.c_uint32)]
+
+
+class GbdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gbd error {code}: {msg}")
+        self.code = code
+
+
+def _declare(lib):
+    vp, u64, u32, ci = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "gbd_default_params": ([ctypes.POINTER(GbdParams)], None),
+        "gbd_create": ([pp, ci, ctypes.POINTER(GbdParams)], ci),
+        "gbd_destroy": ([vp], None),
+        "gbd_load_reads": ([vp, vp, vp, u64, pp, vp], ci),
+        "gbd_free_set": ([vp], None),
+        "gbd_set_size": ([vp], u64),
+        "gbd_set_max_len": ([vp], u32),
+        "gbd_set_pair_cells": ([vp], ctypes.c_double),
+        "gbd_all_pairs": ([vp, vp, vp, u64, vp], ci),
+        "gbd_tile": ([vp, vp, u64, u64, vp, u64, u64, vp, u64, vp], ci),
+        "gbd_batch": ([vp, vp, u64, vp, vp], ci),
+        "gbd_server_create": ([vp, vp, pp], ci),
+        "gbd_server_submit": ([vp, vp, vp, u64, vp, ctypes.POINTER(u64)], ci),
+        "gbd_server_poll": ([vp, u64, ctypes.POINTER(ci)], ci),
+        "gbd_server_wait": ([vp, u64], ci),
+        "gbd_server_destroy": ([vp], None),
+        "gbd_last_error": ([], ctypes.c_char_p),
+        "gbd_probe_op_rate": ([ci, u32, ctypes.POINTER(ctypes.c_double), vp], ci),
+        "gbd_kernel_launches": ([], u64),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+def load_library(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1803_02272_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    return _declare(ctypes.CDLL(path))
+
+
+_lib = load_library()
+
+
+def _check(rc: int):
+    if rc != GBD_OK:
+        raise GbdError(rc, (_lib.gbd_last_error() or b"").decode())
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s) -> int:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ------------------------------------------------------------------ C names
+
+def gbd_default_params() -> GbdParams:
+    p = GbdParams()
+    _lib.gbd_default_params(ctypes.byref(p))
+    return p
+
+
+def gbd_create(device: int = 0, params: GbdParams | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.gbd_create(ctypes.byref(h), device, ctypes.byref(params) if params else None))
+    return h.value
+
+
+def gbd_destroy(ctx: int) -> None:
+    _lib.gbd_destroy(ctx)
+
+
+def gbd_load_reads(ctx: int, seq, offsets, n: int, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.gbd_load_reads(ctx, _ptr(seq), _ptr(offsets), n, ctypes.byref(h), _stream(stream)))
+    return h.value
+
+
+def gbd_free_set(s: int) -> None:
+    _lib.gbd_free_set(s)
+
+
+def gbd_set_size(s: int) -> int:
+    return _lib.gbd_set_size(s)
+
+
+def gbd_set_max_len(s: int) -> int:
+    return _lib.gbd_set_max_len(s)
+
+
+def gbd_set_pair_cells(s: int) -> float:
+    return _lib.gbd_set_pair_cells(s)
+
+
+def gbd_all_pairs(ctx: int, s: int, d_tri, tri_len: int, stream=None) -> None:
+    _check(_lib.gbd_all_pairs(ctx, s, _ptr(d_tri), tri_len, _stream(stream)))
+
+
+def gbd_tile(ctx: int, A: int, a0: int, a1: int, B: int, b0: int, b1: int, d_out, ld: int,
+             stream=None) -> None:
+    _check(_lib.gbd_tile(ctx, A, a0, a1, B, b0, b1, _ptr(d_out), ld, _stream(stream)))
+
+
+def gbd_batch(ctx: int, samples, d_tris, stream=None) -> None:
+    ns = len(samples)
+    arr_s = (ctypes.c_void_p * max(ns, 1))(*samples)
+    arr_o = (ctypes.c_void_p * max(ns, 1))(*[_ptr(t) for t in d_tris])
+    _check(_lib.gbd_batch(ctx, ctypes.cast(arr_s, ctypes.c_void_p), ns,
+                          ctypes.cast(arr_o, ctypes.c_void_p), _stream(stream)))
+
+
+def gbd_server_create(ctx: int, ref: int) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.gbd_server_create(ctx, ref, ctypes.byref(h)))
+    return h.value
+
+
+def gbd_server_submit(srv: int, seq, offsets, nq: int, d_rows) -> int:
+    t = ctypes.c_uint64()
+    _check(_lib.gbd_server_submit(srv, _ptr(seq), _ptr(offsets), nq, _ptr(d_rows), ctypes.byref(t)))
+    return t.value
+
+
+def gbd_server_poll(srv: int, ticket: int) -> bool:
+    d = ctypes.c_int()
+    _check(_lib.gbd_server_poll(srv, ticket, ctypes.byref(d)))
+    return bool(d.value)
+
+
+def gbd_server_wait(srv: int, ticket: int) -> None:
+    _check(_lib.gbd_server_wait(srv, ticket))
+
+
+def gbd_server_destroy(srv: int) -> None:
+    _lib.gbd_server_destroy(srv)
+
+
+def gbd_last_error() -> str:
+    return (_lib.gbd_last_error() or b"").decode()
+
+
+def gbd_probe_op_rate(op: int, iters: int, stream=None) -> float:
+    r = ctypes.c_double()
+    _check(_lib.gbd_probe_op_rate(op, iters, ctypes.byref(r), _stream(stream)))
+    return r.value
+
+
+def gbd_kernel_launches() -> int:
+    return _lib.gbd_kernel_launches()
+
+
+# ------------------------------------------------------------------ convenience wrappers
+
+class ReadSetHandle:
+    """Owns a gbd_set; frees it when garbage collected."""
+
+    def __init__(self, ctx: "Context", handle: int):
+        self.ctx, self.handle = ctx, handle
+
+    @property
+    def n(self) -> int:
+        return gbd_set_size(self.handle)
+
+    @property
+    def max_len(self) -> int:
+        return gbd_set_max_len(self.handle)
+
+    @property
+    def pair_cells(self) -> float:
+        return gbd_set_pair_cells(self.handle)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                gbd_free_set(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+class Context:
+    """A gbd context with torch-allocated outputs."""
+
+    def __init__(self, device: int = 0, **params):
+        p = gbd_default_params()
+        for k, v in params.items():
+            setattr(p, k, v)
+        self.device = device
+        self.handle = gbd_create(device, p)
+
+    def load_reads(self, seq, offsets, stream=None) -> ReadSetHandle:
+        n = len(offsets) - 1
+        return ReadSetHandle(self, gbd_load_reads(self.handle, seq, offsets, n, stream))
+
+    def load(self, readset, stream=None) -> ReadSetHandle:
+        """Load a synth.ReadSet (host numpy arrays)."""
+        seq = np.ascontiguousarray(readset.seq, dtype=np.uint8)
+        off = np.ascontiguousarray(readset.offsets, dtype=np.uint64)
+        if seq.size == 0:
+            seq = np.zeros(1, np.uint8)
+        return self.load_reads(seq, off, stream)
+
+    def all_pairs(self, s: ReadSetHandle, out=None, stream=None):
+        import torch
+        n = s.n
+        m = n * (n - 1) // 2
+        if out is None:
+            out = torch.empty(max(m, 1), dtype=torch.int16, device=f"cuda:{self.device}")
+        gbd_all_pairs(self.handle, s.handle, out, m, stream)
+        return out[:m]
+
+    def tile(self, A: ReadSetHandle, a0, a1, B: ReadSetHandle, b0, b1, out=None, ld=None,
+             stream=None):
+        import torch
+        ld = (b1 - b0) if ld is None else ld
+        if out is None:
+            out = torch.empty(max((a1 - a0) * ld, 1), dtype=torch.int16,
+                              device=f"cuda:{self.device}")
+        gbd_tile(self.handle, A.handle, a0, a1, B.handle, b0, b1, out, ld, stream)
+        return out[: (a1 - a0) * ld].view(a1 - a0, ld)
+
+    def batch(self, sets, outs=None, stream=None):
+        import torch
+        if outs is None:
+            outs = [torch.empty(max(s.n * (s.n - 1) // 2, 1), dtype=torch.int16,
+                                device=f"cuda:{self.device}") for s in sets]
+        gbd_batch(self.handle, [s.handle for s in sets], outs, stream)
+        return [o[: s.n * (s.n - 1) // 2] for o, s in zip(outs, sets)]
+
+    def close(self):
+        if self.handle:
+            gbd_destroy(self.handle)
+            self.handle = None
+
+
+def as_uint16(t) -> np.ndarray:
+    """Host numpy uint16 view of an int16 torch tensor holding uint16 distances."""
+    return t.cpu().numpy().view(np.uint16)

@@ -222,10 +222,11 @@ def paper_scale_ancestors(seed: int = 1003) -> np.ndarray:
     return ancestor_tree(Stream(seed, 0), 450)
 
 
-def workload_paper_scale(seed: int = 1003, n: int = 100_000) -> ReadSet:
+def workload_paper_scale(seed: int = 1003, n: int = 100_000, len_lo: int = 250,
+                         len_hi: int = 450) -> ReadSet:
     """10^5 reads, lengths U[250,450], from the 200 tree ancestors; 5 % sub, 1.5 % indel."""
     anc = paper_scale_ancestors(seed)
-    return reads_from_ancestors(Stream(seed, 1), anc, n, 250, 450, 0.05, 0.015)
+    return reads_from_ancestors(Stream(seed, 1), anc, n, len_lo, len_hi, 0.05, 0.015)
 
 
 def workload_batched(seed: int = 1004, n_samples: int = 64, n_lo: int = 500,

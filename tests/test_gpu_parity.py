@@ -1,0 +1,226 @@
+"""CUDA path vs the CPU oracle, element by element (GPU).
+
+Distances are integers, so the bar is bit-exact equality on every compared pair.
+Every call goes through the C ABI (libgbd.so) via the thin binding.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_02272_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = ["auto", "general", "systolic"]
+
+
+@pytest.fixture(scope="module")
+def gbd():
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1803_02272_gb300 import gbd as g
+    return g
+
+
+def _ctx(gbd, kernel="auto", **kw):
+    k = {"auto": gbd.GBD_KERNEL_AUTO, "general": gbd.GBD_KERNEL_GENERAL,
+         "systolic": gbd.GBD_KERNEL_SYSTOLIC}[kernel]
+    return gbd.Context(0, kernel=k, **kw)
+
+
+def _all_pairs(gbd, ctx, rs):
+    import torch
+    s = ctx.load(rs)
+    out = ctx.all_pairs(s)
+    torch.cuda.synchronize()
+    return gbd.as_uint16(out)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_small_workload_all_pairs_exact(gbd, kernel):
+    """150 reads (lengths 280-320): all 11,175 distances bit-exact."""
+    rs = synth.workload_plain_small()
+    got = _all_pairs(gbd, _ctx(gbd, kernel), rs)
+    want = oracle.all_pairs(rs)
+    assert got.shape == want.shape == (11175,)
+    np.testing.assert_array_equal(got, want)
+
+
+def _edge_reads():
+    st = synth.Stream(4242, 0)
+    reads = ["", "A", "C", "ACGT", "A" * 15, "A" * 16, "A" * 17, "T" * 31, "T" * 32, "T" * 33,
+             "ACGT" * 8, "acgtACGT" * 3, "G" * 64]
+    for L in [1, 2, 3, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257,
+              300, 449, 450, 511, 512, 513, 700]:
+        reads.append("".join("ACGT"[c] for c in synth.random_codes(st, (L,))))
+    base = "".join("ACGT"[c] for c in synth.random_codes(st, (400,)))
+    reads += [base, base[:200], base[100:350], base[::-1]]
+    return reads
+
+
+@pytest.mark.parametrize("kernel", ["auto", "general"])
+def test_edge_lengths_exact(gbd, kernel):
+    """Empty reads, word-boundary lengths (15/16/17, 31/32/33...), homopolymers, a read
+    inside another, lengths around 512 and beyond (those pairs go to the general kernel)."""
+    rs = synth.from_strings(_edge_reads())
+    got = _all_pairs(gbd, _ctx(gbd, kernel), rs)
+    np.testing.assert_array_equal(got, oracle.all_pairs(rs))
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 33])
+def test_tiny_sets(gbd, n):
+    rs = synth.workload_plain_small().subset(range(n))
+    ctx = _ctx(gbd)
+    got = _all_pairs(gbd, ctx, rs) if n >= 2 else None
+    if n >= 2:
+        np.testing.assert_array_equal(got, oracle.all_pairs(rs))
+    else:
+        s = ctx.load(rs)
+        assert s.n == n
+        gbd.gbd_all_pairs(ctx.handle, s.handle, None, 0)
+
+
+def test_tile_rectangle_exact(gbd):
+    import torch
+    rs = synth.workload_plain_10k(n=400)
+    ctx = _ctx(gbd)
+    A = ctx.load(rs.subset(range(0, 150)))
+    B = ctx.load(rs.subset(range(150, 400)))
+    out = ctx.tile(A, 7, 140, B, 3, 241, ld=250)
+    torch.cuda.synchronize()
+    got = gbd.as_uint16(out)[:, :238]
+    want = oracle.rect(rs.subset(range(0, 150)), 7, 140, rs.subset(range(150, 400)), 3, 241)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_symmetry_tile_both_orders(gbd):
+    import torch
+    rs = synth.workload_plain_10k(n=300)
+    ctx = _ctx(gbd)
+    A = ctx.load(rs.subset(range(0, 120)))
+    B = ctx.load(rs.subset(range(120, 300)))
+    ab = gbd.as_uint16(ctx.tile(A, 0, 120, B, 0, 180))
+    ba = gbd.as_uint16(ctx.tile(B, 0, 180, A, 0, 120))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(ab, ba.T)
+
+
+def test_invalid_byte_rejected(gbd):
+    ctx = _ctx(gbd)
+    rs = synth.from_strings(["ACGT", "ACNT", "GG"])
+    with pytest.raises(gbd.GbdError) as ei:
+        ctx.load(rs)
+    assert ei.value.code == gbd.GBD_EINVAL
+    assert "position 6" in gbd.gbd_last_error()
+
+
+def test_wrong_triangle_length_rejected(gbd):
+    import torch
+    ctx = _ctx(gbd)
+    s = ctx.load(synth.workload_plain_small().subset(range(10)))
+    out = torch.empty(44, dtype=torch.int16, device="cuda:0")
+    with pytest.raises(gbd.GbdError) as ei:
+        gbd.gbd_all_pairs(ctx.handle, s.handle, out, 44)
+    assert ei.value.code == gbd.GBD_EINVAL
+
+
+def test_device_input_pointers(gbd):
+    """Reads given as device tensors (torch) instead of host arrays."""
+    import torch
+    rs = synth.workload_plain_small().subset(range(40))
+    ctx = _ctx(gbd)
+    seq = torch.from_numpy(rs.seq).cuda()
+    off = torch.from_numpy(rs.offsets.astype(np.int64)).cuda()
+    s = ctx.load_reads(seq, off)
+    tri = gbd.as_uint16(ctx.all_pairs(s))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(tri, oracle.all_pairs(rs))
+
+
+@pytest.mark.parametrize("scores", [(2, -3, 2), (1, -2, 3)])
+def test_other_scores_raw_score_mode(gbd, scores):
+    m, x, g = scores
+    rs = synth.workload_plain_small().subset(range(30))
+    ctx = _ctx(gbd, "auto", match=m, mismatch=x, gap=g, conversion=gbd.GBD_CONV_SCORE)
+    got = _all_pairs(gbd, ctx, rs)
+    n = rs.n
+    pi, pj = np.triu_indices(n, 1)
+    want = oracle.pair_scores(rs, pi, pj, match=m, mismatch=x, gap=g)
+    np.testing.assert_array_equal(got.astype(np.int64), want)
+
+
+def test_batch_matches_per_sample(gbd):
+    import torch
+    samples = synth.workload_batched(n_samples=5, n_lo=20, n_hi=120)
+    ctx = _ctx(gbd)
+    sets = [ctx.load(s) for s in samples]
+    outs = ctx.batch(sets)
+    torch.cuda.synchronize()
+    for rs, o in zip(samples, outs):
+        np.testing.assert_array_equal(gbd.as_uint16(o), oracle.all_pairs(rs))
+
+
+def test_10k_workload_sampled(gbd):
+    """10^4 reads (5.0e7 pairs): the whole triangle on the GPU, 20,000 seeded pairs
+    checked against the oracle, plus every pair of the first and last 40 reads."""
+    import torch
+    rs = synth.workload_plain_10k()
+    n = rs.n
+    ctx = _ctx(gbd)
+    s = ctx.load(rs)
+    tri = gbd.as_uint16(ctx.all_pairs(s))
+    torch.cuda.synchronize()
+    st = synth.Stream(5151, 0)
+    i = st.integers(0, n - 2, (20000,))
+    j = i + 1 + np.floor(st.uniform((20000,)) * (n - 1 - i)).astype(np.int64)
+    k = i * n - i * (i + 1) // 2 + (j - i - 1)
+    np.testing.assert_array_equal(tri[k], oracle.pairs(rs, i, j))
+    for block in (range(0, 40), range(n - 40, n)):
+        b = np.array(block)
+        bi, bj = np.triu_indices(len(b), 1)
+        ii, jj = b[bi], b[bj]
+        kk = ii * n - ii * (ii + 1) // 2 + (jj - ii - 1)
+        np.testing.assert_array_equal(tri[kk], oracle.pairs(rs, ii, jj))
+
+
+def test_systolic_every_rows_per_lane():
+    """Query lengths 1..512 cover every rows-per-lane variant (R = 1..16) of the
+    systolic kernel, with subjects shorter and longer than the query."""
+    import torch
+    from paper_1803_02272_gb300 import gbd as g
+    st = synth.Stream(8080, 0)
+    reads = []
+    for L in list(range(1, 40)) + [63, 64, 65, 95, 96, 97] + list(range(100, 513, 29)) + [511, 512]:
+        reads.append("".join("ACGT"[c] for c in synth.random_codes(st, (L,))))
+    base = reads[-1]
+    reads += [base[5:300], base[:128] + "ACGT" * 10, base[200:]]
+    rs = synth.from_strings(reads)
+    ctx = _ctx(g, "systolic")
+    got = _all_pairs(g, ctx, rs)
+    np.testing.assert_array_equal(got, oracle.all_pairs(rs))
+
+
+def test_long_subject_rebases():
+    """A 20,000-base subject streams past short queries: the DP values are rebased many
+    times inside one subject."""
+    import torch
+    from paper_1803_02272_gb300 import gbd as g
+    st = synth.Stream(9090, 0)
+    long = "".join("ACGT"[c] for c in synth.random_codes(st, (20000,)))
+    reads = [long[1000:1300], long[15000:15450], long[19900:], "ACGT" * 50, long]
+    rs = synth.from_strings(reads)
+    got = _all_pairs(g, _ctx(g, "auto"), rs)
+    np.testing.assert_array_equal(got, oracle.all_pairs(rs))
+    ctx = _ctx(g, "auto")
+    A = ctx.load(rs.subset([0, 1, 2, 3]))
+    B = ctx.load(rs.subset([4, 4, 0]))
+    out = ctx.tile(A, 0, 4, B, 0, 3)
+    torch.cuda.synchronize()
+    want = oracle.rect(rs.subset([0, 1, 2, 3]), 0, 4, rs.subset([4, 4, 0]), 0, 3)
+    np.testing.assert_array_equal(g.as_uint16(out), want)
+
+
+def test_systolic_rejects_other_scores(gbd):
+    with pytest.raises(gbd.GbdError) as ei:
+        gbd.Context(0, kernel=gbd.GBD_KERNEL_SYSTOLIC, match=2)
+    assert ei.value.code == gbd.GBD_EINVAL
