@@ -122,6 +122,27 @@ int gbd_server_poll(gbd_server *srv, uint64_t ticket, int *done);
 int gbd_server_wait(gbd_server *srv, uint64_t ticket);
 void gbd_server_destroy(gbd_server *srv);
 
+/* Allocation-free rectangle.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- code whose device memory is owned by another
+ * allocator (a framework's caching pool or a pre-reserved arena, where a direct cudaMalloc
+ * fails or fragments it) or code paths that must not allocate at all.
+ *   d_out[i*ld + j] = d(A[i], B[j]) for i < nA, j < nB, with the context's scores.
+ *   Inputs are DEVICE pointers owned by the caller: read bytes and nA+1 / nB+1 offsets as
+ *   for gbd_load_reads; every read must be at most max_len (<= 65535) bases long.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch (flags, the
+ * 2-bit packed reads, the DP boundary rows) is one static device array of 32 MiB that
+ * every GPU loading the library holds until the process exits; inputs whose packed form
+ * plus one thread block's boundary rows do not fit return GBD_EINVAL.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) and should come
+ * before any stream capture.  All calls share the one array and the call synchronises
+ * `stream` once to read its validation flags; calls that overlap on the GPU (other
+ * streams, other host threads) race on the array and must be serialised by the caller.
+ * Errors: EINVAL for a non-ACGT byte, a read longer than max_len, decreasing offsets,
+ * ld < nB, or inputs too large for the array. */
+int gbd_tile_noalloc(gbd_ctx *ctx, const uint8_t *d_seqA, const uint64_t *d_offA, uint64_t nA,
+                     const uint8_t *d_seqB, const uint64_t *d_offB, uint64_t nB,
+                     uint32_t max_len, uint16_t *d_out, uint64_t ld, void *stream);
+
 /* Thread-local text of the last error raised on the calling thread ("" if none). */
 const char *gbd_last_error(void);
 

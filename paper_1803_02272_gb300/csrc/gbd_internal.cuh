@@ -119,6 +119,10 @@ struct GeneralJob {
     uint64_t nrows = 0;
 };
 int run_general(const GeneralJob &job, const Scoring &sc, int sm_count, cudaStream_t stream);
+// Same kernel on a rectangle job, with boundary rows in caller-provided scratch
+// (scratch_ints ints); allocates nothing.
+int run_general_in(const GeneralJob &job, const Scoring &sc, int *scratch, uint64_t scratch_ints,
+                   int sm_count, cudaStream_t stream);
 
 // Instruction-rate probe.
 int probe_op_rate(int op, uint32_t iters, double *rate, int sm_count, cudaStream_t stream);

@@ -150,4 +150,25 @@ int run_general(const GeneralJob &job, const Scoring &sc, int sm_count, cudaStre
     return GBD_OK;
 }
 
+int run_general_in(const GeneralJob &job, const Scoring &sc, int *scratch, uint64_t scratch_ints,
+                   int sm_count, cudaStream_t stream)
+{
+    if (job.mode != OUT_RECT || job.rows) return fail(GBD_EINVAL, "internal: rectangle jobs only");
+    const uint64_t units = (job.a1 - job.a0) * (job.b1 - job.b0);
+    if (units == 0) return GBD_OK;
+    const int threads = 128;
+    const uint64_t per_thread = (uint64_t)job.B.stride * kBasesPerWord + 1;   // ints
+    uint64_t blocks = (uint64_t)std::max(sm_count, 1) * 8;
+    while (blocks > 0 && blocks * threads * per_thread > scratch_ints) --blocks;
+    if (blocks == 0)
+        return fail(GBD_EINVAL, "the boundary rows of one thread block do not fit the scratch area");
+    const uint64_t need_blocks = (units + threads - 1) / threads;
+    if (blocks > need_blocks) blocks = need_blocks;
+    sw_general_kernel<<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units);
+    note_launches(1);
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) return cuda_fail(le, "sw_general_kernel launch");
+    return GBD_OK;
+}
+
 }  // namespace gbd

@@ -32,7 +32,7 @@ EXPORTS = [
     "gbd_set_size", "gbd_set_max_len", "gbd_set_pair_cells", "gbd_all_pairs", "gbd_tile",
     "gbd_batch", "gbd_server_create", "gbd_server_submit", "gbd_server_poll",
     "gbd_server_wait", "gbd_server_destroy", "gbd_last_error", "gbd_probe_op_rate",
-    "gbd_kernel_launches",
+    "gbd_kernel_launches", "gbd_tile_noalloc",
 ]
 
 
@@ -72,6 +72,7 @@ def _declare(lib):
         "gbd_last_error": ([], ctypes.c_char_p),
         "gbd_probe_op_rate": ([ci, u32, ctypes.POINTER(ctypes.c_double), vp], ci),
         "gbd_kernel_launches": ([], u64),
+        "gbd_tile_noalloc": ([vp, vp, vp, u64, vp, vp, u64, u32, vp, u64, vp], ci),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -207,6 +208,13 @@ def gbd_probe_op_rate(op: int, iters: int, stream=None) -> float:
     r = ctypes.c_double()
     _check(_lib.gbd_probe_op_rate(op, iters, ctypes.byref(r), _stream(stream)))
     return r.value
+
+
+def gbd_tile_noalloc(ctx: int, seqA, offA, nA: int, seqB, offB, nB: int, max_len: int, d_out,
+                     ld: int, stream=None) -> None:
+    """Allocation-free rectangle (device inputs and output; see include/gbd.h)."""
+    _check(_lib.gbd_tile_noalloc(ctx, _ptr(seqA), _ptr(offA), nA, _ptr(seqB), _ptr(offB), nB,
+                                 max_len, _ptr(d_out), ld, _stream(stream)))
 
 
 def gbd_kernel_launches() -> int:
