@@ -46,6 +46,7 @@ struct SysPlan {
     std::vector<Bucket> buckets;
     void *d_buf = nullptr;
     bool stream_ordered = false;   // d_buf from cudaMallocAsync (freed on a stream)
+    uint32_t piece = 1024;         // subjects per work unit
     uint64_t units() const
     {
         uint64_t u = 0;

@@ -419,7 +419,7 @@ template <int R>
 __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 7)
 sw_systolic_kernel(const SysJob *__restrict__ jobs, const SysEntry *__restrict__ entries,
                    const uint32_t *__restrict__ prefix, uint32_t nentries, uint32_t nunits,
-                   uint32_t *counter, uint32_t *err)
+                   uint32_t piece_len, uint32_t *counter, uint32_t *err)
 {
     extern __shared__ uint32_t smem[];
     const int warp = threadIdx.x >> 5;
@@ -443,8 +443,8 @@ sw_systolic_kernel(const SysJob *__restrict__ jobs, const SysEntry *__restrict__
         SysUnit u;
         u.job = en.job;
         u.q = en.q;
-        u.sub_begin = en.sub_begin + piece * kSystolicPiece;
-        u.nsub = min(kSystolicPiece, en.nsub - piece * kSystolicPiece);
+        u.sub_begin = en.sub_begin + piece * piece_len;
+        u.nsub = min(piece_len, en.nsub - piece * piece_len);
         run_unit<R>(jobs[u.job], u, ws, lane, err);
         __syncwarp();
     }
@@ -452,8 +452,8 @@ sw_systolic_kernel(const SysJob *__restrict__ jobs, const SysEntry *__restrict__
 
 template <int R>
 int launch_bucket(const SysJob *d_jobs, const SysEntry *entries, const uint32_t *prefix,
-                  uint32_t nentries, uint32_t nunits, uint32_t *counter, uint32_t *err,
-                  int sm_count, cudaStream_t stream)
+                  uint32_t nentries, uint32_t nunits, uint32_t piece_len, uint32_t *counter,
+                  uint32_t *err, int sm_count, cudaStream_t stream)
 {
     const size_t smem = systolic_smem_bytes();
     static bool attr_set = false;
@@ -470,7 +470,7 @@ int launch_bucket(const SysJob *d_jobs, const SysEntry *entries, const uint32_t 
     const uint64_t need = (nunits + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
     if (blocks > need) blocks = need;
     sw_systolic_kernel<R><<<(unsigned)blocks, WARPS_PER_BLOCK * 32, smem, stream>>>(
-        d_jobs, entries, prefix, nentries, nunits, counter, err);
+        d_jobs, entries, prefix, nentries, nunits, piece_len, counter, err);
     note_launches(1);
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) return cuda_fail(le, "sw_systolic_kernel launch");
@@ -482,9 +482,11 @@ int launch_bucket(const SysJob *d_jobs, const SysEntry *entries, const uint32_t 
 size_t systolic_smem_bytes() { return (size_t)WARPS_PER_BLOCK * WARP_WORDS * sizeof(uint32_t); }
 
 int build_plan(const std::vector<SysEntry> &entries, const std::vector<uint8_t> &rows,
-               SysPlan &plan, bool persistent, cudaStream_t stream)
+               SysPlan &plan, bool persistent, cudaStream_t stream, uint32_t piece_len)
 {
     plan = SysPlan{};
+    if (piece_len == 0) return fail(GBD_EINVAL, "internal: zero piece length");
+    plan.piece = piece_len;
     std::vector<std::vector<SysEntry>> by_r(17);
     for (size_t i = 0; i < entries.size(); ++i) {
         if (entries[i].nsub == 0) continue;
@@ -505,7 +507,7 @@ int build_plan(const std::vector<SysEntry> &entries, const std::vector<uint8_t> 
         uint64_t acc = 0;
         for (uint32_t e = 0; e < b.nentries; ++e) {
             pf[e] = (uint32_t)acc;
-            acc += (by_r[R][e].nsub + kSystolicPiece - 1) / kSystolicPiece;
+            acc += (by_r[R][e].nsub + piece_len - 1) / piece_len;
         }
         if (acc >= 0xffffffffull) return fail(GBD_EINVAL, "too many work units for one launch");
         pf[b.nentries] = (uint32_t)acc;
@@ -558,7 +560,7 @@ int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaSt
         const uint32_t *pf = reinterpret_cast<const uint32_t *>(base + b.prefix_off);
         uint32_t *ctr = scratch + 2 * i, *err = scratch + 2 * i + 1;
         switch (b.R) {
-#define GBD_CASE(RR) case RR: rc = launch_bucket<RR>(d_jobs, en, pf, b.nentries, b.nunits, ctr, err, sm_count, stream); break;
+#define GBD_CASE(RR) case RR: rc = launch_bucket<RR>(d_jobs, en, pf, b.nentries, b.nunits, plan.piece, ctr, err, sm_count, stream); break;
             GBD_CASE(1) GBD_CASE(2) GBD_CASE(3) GBD_CASE(4) GBD_CASE(5) GBD_CASE(6) GBD_CASE(7)
             GBD_CASE(8) GBD_CASE(9) GBD_CASE(10) GBD_CASE(11) GBD_CASE(12) GBD_CASE(13)
             GBD_CASE(14) GBD_CASE(15) GBD_CASE(16)
@@ -572,4 +574,12 @@ int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaSt
     return GBD_OK;
 }
 
+}  // namespace gbd
+
+namespace gbd {
+int systolic_resident_warps(int sm_count)
+{
+    // 7 blocks of 2 warps per SM (shared memory bound, see launch_bucket)
+    return sm_count * 7 * WARPS_PER_BLOCK;
+}
 }  // namespace gbd

@@ -7,7 +7,7 @@ namespace gbd {
 
 // Reads up to this length can be the query (row) read of a systolic work unit.
 constexpr int kSystolicMaxQuery = 512;
-// Work units cover at most this many subjects (bounds the tail of every launch).
+// Default number of subjects per work unit (bounds the tail of every launch).
 constexpr uint32_t kSystolicPiece = 1024;
 
 // One output problem: queries of Q against subjects of S.
@@ -22,7 +22,7 @@ struct SysJob {
 };
 
 // One query (original index q in Q, length <= 512) against the subjects at list
-// positions [sub_begin, sub_begin + nsub); split into units of kSystolicPiece subjects.
+// positions [sub_begin, sub_begin + nsub); split into units of plan.piece subjects.
 struct SysEntry {
     uint32_t job, q, sub_begin, nsub;
 };
@@ -34,7 +34,10 @@ inline int systolic_rows(int la) { return la <= 32 ? 1 : (la + 31) / 32; }
 // order inside a bucket (callers put the largest first).  persistent: cudaMalloc (kept
 // with a read set) instead of stream-ordered memory.
 int build_plan(const std::vector<SysEntry> &entries, const std::vector<uint8_t> &rows,
-               SysPlan &plan, bool persistent, cudaStream_t stream);
+               SysPlan &plan, bool persistent, cudaStream_t stream,
+               uint32_t piece_len = kSystolicPiece);
+// Number of warps the systolic kernel keeps resident on the whole GPU.
+int systolic_resident_warps(int sm_count);
 void free_plan(SysPlan &plan, cudaStream_t stream);
 
 int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaStream_t stream);

@@ -305,6 +305,44 @@ class Context:
             self.handle = None
 
 
+class Server:
+    """A serving loop over a resident reference set (gbd_server_*)."""
+
+    def __init__(self, ctx: Context, ref: ReadSetHandle):
+        self.ctx, self.ref = ctx, ref
+        self.handle = gbd_server_create(ctx.handle, ref.handle)
+
+    def submit(self, readset, out=None):
+        """Queue a synth.ReadSet of queries; returns (ticket, output tensor nq x n_ref)."""
+        import torch
+        seq = np.ascontiguousarray(readset.seq, dtype=np.uint8)
+        if seq.size == 0:
+            seq = np.zeros(1, np.uint8)
+        off = np.ascontiguousarray(readset.offsets, dtype=np.uint64)
+        nq = len(off) - 1
+        if out is None:
+            out = torch.empty((nq, self.ref.n), dtype=torch.int16, device=f"cuda:{self.ctx.device}")
+        t = gbd_server_submit(self.handle, seq, off, nq, out)
+        return t, out
+
+    def poll(self, ticket: int) -> bool:
+        return gbd_server_poll(self.handle, ticket)
+
+    def wait(self, ticket: int) -> None:
+        gbd_server_wait(self.handle, ticket)
+
+    def close(self):
+        if self.handle:
+            gbd_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def as_uint16(t) -> np.ndarray:
     """Host numpy uint16 view of an int16 torch tensor holding uint16 distances."""
     return t.cpu().numpy().view(np.uint16)

@@ -1,0 +1,127 @@
+"""Serving (continuous batching over a resident reference set) vs the oracle (GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_02272_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1803_02272_gb300 import gbd
+    ref_rs = synth.workload_plain_10k(n=3000)
+    ctx = gbd.Context(0)
+    ref = ctx.load(ref_rs)
+    return gbd, ctx, ref, ref_rs
+
+
+def _queries(seed, sizes):
+    reqs = synth.workload_served_queries(len(sizes), rate_per_s=100.0, seed=seed, nq_hi=8)
+    out = []
+    for q, n in zip(reqs, sizes):
+        st = synth.Stream(seed, n)
+        anc = synth.random_codes(st, (3, 450))
+        out.append(synth.reads_from_ancestors(st, anc, n, 250, 450, 0.05, 0.015))
+    return out
+
+
+def test_single_request_matches_oracle(env):
+    import torch
+    gbd, ctx, ref, ref_rs = env
+    srv = gbd.Server(ctx, ref)
+    q = _queries(1, [5])[0]
+    t, out = srv.submit(q)
+    srv.wait(t)
+    torch.cuda.synchronize()
+    got = gbd.as_uint16(out)
+    cols = np.arange(0, ref_rs.n, 7)
+    want = oracle.rect(q, 0, q.n, ref_rs.subset(cols), 0, len(cols))
+    np.testing.assert_array_equal(got[:, cols], want)
+    srv.close()
+
+
+def test_rows_identical_alone_and_mixed(env):
+    """Each request's rows are byte-identical whether it runs alone or among others."""
+    import torch
+    gbd, ctx, ref, ref_rs = env
+    qs = _queries(2, [1, 17, 3, 64, 9, 2])
+    srv = gbd.Server(ctx, ref)
+    alone = []
+    for q in qs:
+        t, out = srv.submit(q)
+        srv.wait(t)
+        alone.append(gbd.as_uint16(out).copy())
+    tickets = [srv.submit(q) for q in qs]             # all at once: admitted together
+    done = [False] * len(qs)
+    while not all(done):
+        for i, (t, _) in enumerate(tickets):
+            if not done[i]:
+                done[i] = srv.poll(t)
+    torch.cuda.synchronize()
+    for a, (_, out) in zip(alone, tickets):
+        np.testing.assert_array_equal(gbd.as_uint16(out), a)
+    # and every row against the regular rectangle entry point
+    for q, a in zip(qs, alone):
+        qs_h = ctx.load(q)
+        ref_rows = gbd.as_uint16(ctx.tile(qs_h, 0, q.n, ref, 0, ref.n))
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(a, ref_rows)
+    srv.close()
+
+
+def test_budget_rejects_and_queues(env):
+    import torch
+    gbd, _, _, ref_rs = env
+    per_query = ref_rs.n * 2
+    ctx = gbd.Context(0, hbm_budget=int(per_query * 40))
+    ref = ctx.load(ref_rs)
+    srv = gbd.Server(ctx, ref)
+    big = _queries(3, [64])[0]                        # 64 rows never fit a 40-row budget
+    with pytest.raises(gbd.GbdError) as ei:
+        srv.submit(big)
+    assert ei.value.code == gbd.GBD_EBUDGET
+    small = _queries(4, [30, 30, 30])                 # fit one at a time: they queue
+    tk = [srv.submit(q) for q in small]
+    for t, _ in tk:
+        srv.wait(t)
+    torch.cuda.synchronize()
+    for q, (_, out) in zip(small, tk):
+        cols = np.arange(0, ref_rs.n, 97)
+        want = oracle.rect(q, 0, q.n, ref_rs.subset(cols), 0, len(cols))
+        np.testing.assert_array_equal(gbd.as_uint16(out)[:, cols], want)
+    srv.close()
+
+
+def test_wait_timeout_then_completion(env):
+    """A wait with a tiny limit returns ETIMEDOUT (host-side bound), the ticket stays
+    valid and the request completes later."""
+    import torch
+    gbd, _, _, ref_rs = env
+    ctx = gbd.Context(0, timeout_us=1)
+    ref = ctx.load(ref_rs)
+    srv = gbd.Server(ctx, ref)
+    q = _queries(5, [256])[0]
+    t, out = srv.submit(q)
+    with pytest.raises(gbd.GbdError) as ei:
+        srv.wait(t)
+    assert ei.value.code == gbd.GBD_ETIMEDOUT
+    while not srv.poll(t):
+        pass
+    with pytest.raises(gbd.GbdError) as ei:           # a finished ticket is reported once
+        srv.poll(t)
+    assert ei.value.code == gbd.GBD_ENOTFOUND
+    torch.cuda.synchronize()
+    srv.close()
+
+
+def test_bad_request_rejected(env):
+    gbd, ctx, ref, _ = env
+    srv = gbd.Server(ctx, ref)
+    with pytest.raises(gbd.GbdError) as ei:
+        srv.submit(synth.from_strings(["ACGTN"]))
+    assert ei.value.code == gbd.GBD_EINVAL
+    srv.close()
