@@ -48,6 +48,12 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--mode", choices=["allpairs", "batch", "serve"], default="allpairs")
+    ap.add_argument("--serve-requests", type=int, default=40,
+                    help="requests in the serving phase of the all-pairs run (0 = skip)")
+    ap.add_argument("--serve-load", type=float, default=0.8,
+                    help="offered load of that phase, as a fraction of measured pairs/s")
+    ap.add_argument("--samples", type=int, default=64, help="batch mode: samples")
     return ap.parse_args(argv)
 
 
@@ -364,6 +370,14 @@ def run_gbd(args):
         line["e2e"] = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample(rs, args.cpu_seconds)
+    if args.serve_requests > 0 and rank == 0:
+        # served-batch latency: Poisson arrivals against this set, resident
+        ref = ctx.load(rs)
+        mean_pairs = 492.0 * n             # mean of log-U[1,4096] batch sizes x n_ref
+        rate = args.serve_load * pairs_per_s / mean_pairs
+        line["serving"] = serve_phase(gbd, ctx, ref, rs, dev, args.serve_requests, rate)
+        line["serving"]["offered_load"] = args.serve_load
+        del ref
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(world)
@@ -393,10 +407,157 @@ def run_e2e(gbd, ctx, rs, dev, stream):
             "d2h_bytes_per_step": int(m * 2), "seconds": dt}
 
 
+# ------------------------------------------------------------------ serving and batching
+
+def percentile(xs, p):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), p)) if len(xs) else None
+
+
+def serve_phase(gbd, ctx, ref_handle, ref_rs, dev, n_requests, rate_per_s, seed=1005,
+                check=True, burst=False):
+    """Poisson arrivals of query batches against a resident reference set; returns
+    latency percentiles (submit -> rows complete) and served pairs/s."""
+    import torch
+    from paper_1803_02272_gb300 import synth
+    reqs = synth.workload_served_queries(n_requests, rate_per_s, seed=seed)
+    srv = gbd.Server(ctx, ref_handle)
+    n_ref = ref_rs.n
+    pending, lat, outs = {}, [], []
+    t0 = time.perf_counter()
+    i = 0
+    total_pairs = sum(r.reads.n for r in reqs) * n_ref
+    while i < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and (burst or reqs[i].arrival_s <= now):
+            out = torch.empty((reqs[i].reads.n, n_ref), dtype=torch.int16, device=dev)
+            t, _ = srv.submit(reqs[i].reads, out)
+            pending[t] = (time.perf_counter(), i, out)
+            i += 1
+        for t in list(pending):
+            if srv.poll(t):
+                ts, k, out = pending.pop(t)
+                lat.append(time.perf_counter() - ts)
+                outs.append((k, out))
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    srv.close()
+    torch.cuda.synchronize()
+    mism = None
+    if check:
+        import oracle
+        rng = np.random.default_rng(seed)
+        pi, pj, got = [], [], []
+        q_all = []
+        for k, out in outs:
+            q = reqs[k].reads
+            rows = rng.integers(0, q.n, size=4)
+            cols = rng.integers(0, n_ref, size=4)
+            vals = out[torch.from_numpy(rows).to(dev), torch.from_numpy(cols).to(dev)]
+            vals = vals.cpu().numpy().view(np.uint16)
+            for r_, c_, v_ in zip(rows, cols, vals):
+                q_all.append(q.read(int(r_)))
+                pj.append(int(c_))
+                got.append(int(v_))
+        qs = synth.from_strings(q_all)
+        want = oracle.pairs(qs, np.arange(len(q_all)), np.array(pj), ref_rs)
+        mism = int(np.count_nonzero(want != np.array(got, dtype=np.uint16)))
+    del outs
+    nq = [r.reads.n for r in reqs]
+    return {"requests": len(reqs), "mean_queries": float(np.mean(nq)),
+            "p50_ms": percentile(lat, 50) * 1e3, "p99_ms": percentile(lat, 99) * 1e3,
+            "pairs_per_s": total_pairs / wall, "wall_s": wall,
+            "spot_check_mismatches": mism}
+
+
+def run_batch_mode(args):
+    """64 uneven samples: one gbd_batch call against one gbd_all_pairs call per sample."""
+    import torch
+    from paper_1803_02272_gb300 import gbd, synth
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    samples = synth.workload_batched(n_samples=args.samples)
+    ctx = gbd.Context(0)
+    sets = [ctx.load(s) for s in samples]
+    outs_b = [torch.empty(max(s.n * (s.n - 1) // 2, 1), dtype=torch.int16, device=dev) for s in samples]
+    outs_p = [torch.empty_like(o) for o in outs_b]
+    pairs = sum(s.n * (s.n - 1) // 2 for s in samples)
+    cells = sum(s.total_cells() for s in samples)
+
+    def plain():
+        for st, o in zip(sets, outs_p):
+            ctx.all_pairs(st, out=o)
+
+    def batched():
+        ctx.batch(sets, outs=outs_b)
+
+    res = {}
+    for name, fn in (("plain_per_sample", plain), ("batched", batched)):
+        fn()                                   # warm-up (also builds the schedules)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        t = float(np.median(ts))
+        res[name] = {"seconds": t, "pairs_per_s": pairs / t, "gcups": cells / t / 1e9}
+    same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_p))
+    line = {"mode": "batch", "workload": f"{len(samples)} samples, read counts "
+            f"{min(s.n for s in samples)}-{max(s.n for s in samples)}, lengths U[150,500]",
+            "pairs": pairs, "cells": cells, "identical_outputs": bool(same), **res,
+            "speedup": res["plain_per_sample"]["seconds"] / res["batched"]["seconds"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve_mode(args):
+    """Served queries against a resident paper-scale reference: burst throughput of the
+    server against plain sequential per-request rectangles, then latency under load."""
+    import torch
+    from paper_1803_02272_gb300 import gbd, synth
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    ref_rs = synth.workload_paper_scale(n=args.n)
+    ctx = gbd.Context(0)
+    ref = ctx.load(ref_rs)
+    reqs = synth.workload_served_queries(args.serve_requests, 1.0, seed=1006)
+    total_pairs = sum(r.reads.n for r in reqs) * ref_rs.n
+    # plain: one gbd_tile per request, back to back
+    out = torch.empty((4096, ref_rs.n), dtype=torch.int16, device=dev)
+    q0 = ctx.load(reqs[0].reads)
+    ctx.tile(q0, 0, q0.n, ref, 0, ref.n, out=out.view(-1))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in reqs:
+        qh = ctx.load(r.reads)
+        ctx.tile(qh, 0, qh.n, ref, 0, ref.n, out=out.view(-1))
+    torch.cuda.synchronize()
+    plain_pps = total_pairs / (time.perf_counter() - t0)
+    burst = serve_phase(gbd, ctx, ref, ref_rs, dev, args.serve_requests, 1.0, seed=1006,
+                        check=True, burst=True)
+    loads = {}
+    mean_pairs = total_pairs / len(reqs)
+    for load in (0.5, 0.8, 0.95):
+        rate = load * burst["pairs_per_s"] / mean_pairs
+        loads[str(load)] = serve_phase(gbd, ctx, ref, ref_rs, dev, args.serve_requests, rate,
+                                       seed=2000 + int(load * 100))
+    line = {"mode": "serve", "reference_reads": ref_rs.n, "requests": len(reqs),
+            "plain_sequential_pairs_per_s": plain_pps, "server_burst": burst,
+            "server_under_load": loads,
+            "server_vs_plain": burst["pairs_per_s"] / plain_pps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batch":
+        return run_batch_mode(args)
+    if args.mode == "serve":
+        return run_serve_mode(args)
     return run_gbd(args)
 
 

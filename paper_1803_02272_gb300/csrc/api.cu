@@ -55,38 +55,53 @@ static bool use_systolic(const gbd_ctx *ctx)
     return ctx->params.kernel != GBD_KERNEL_GENERAL && default_scores(ctx->params);
 }
 
-// Length-sorted order of a set and its systolic entries (built once per set).
+// Systolic entries and long-read rows of a set's triangle (built once per set).
 static int build_tri_schedule(gbd_set *set, cudaStream_t st)
 {
     TriSchedule &sc = set->sched;
     if (sc.built) return GBD_OK;
     const uint64_t n = set->n;
-    sc.h_perm.resize(n);
-    std::iota(sc.h_perm.begin(), sc.h_perm.end(), 0u);
-    std::stable_sort(sc.h_perm.begin(), sc.h_perm.end(),
-                     [&](uint32_t x, uint32_t y) { return set->h_len[x] < set->h_len[y]; });
-    uint64_t lb = 0;
-    while (lb < n && set->h_len[sc.h_perm[lb]] <= kSystolicMaxQuery) ++lb;
-    sc.long_begin = lb;
     std::vector<SysEntry> entries;
     std::vector<uint8_t> rows;
-    const uint64_t last = std::min<uint64_t>(lb, n > 0 ? n - 1 : 0);
-    entries.reserve(last);
-    rows.reserve(last);
-    for (uint64_t a = 0; a < last; ++a) {
-        entries.push_back({0u, sc.h_perm[a], (uint32_t)(a + 1), (uint32_t)(n - 1 - a)});
-        rows.push_back((uint8_t)systolic_rows(set->h_len[sc.h_perm[a]]));
+    std::vector<uint32_t> long_rows;
+    std::vector<uint64_t> long_prefix(1, 0);
+    for (uint64_t i = 0; i + 1 < n; ++i) {
+        if (set->h_len[i] <= kSystolicMaxQuery) {
+            entries.push_back({0u, (uint32_t)i, (uint32_t)(i + 1), (uint32_t)(n - 1 - i)});
+            rows.push_back((uint8_t)systolic_rows(set->h_len[i]));
+        } else {
+            long_rows.push_back((uint32_t)i);
+            long_prefix.push_back(long_prefix.back() + (n - 1 - i));
+        }
     }
-    if (n > 0) {
-        GBD_CUDA_TRY(cudaMalloc((void **)&sc.d_perm, n * sizeof(uint32_t)));
-        GBD_CUDA_TRY(cudaMemcpyAsync(sc.d_perm, sc.h_perm.data(), n * sizeof(uint32_t),
+    sc.nlong = long_rows.size();
+    if (sc.nlong) {
+        GBD_CUDA_TRY(cudaMalloc((void **)&sc.d_long_rows, sc.nlong * sizeof(uint32_t)));
+        GBD_CUDA_TRY(cudaMalloc((void **)&sc.d_long_prefix, (sc.nlong + 1) * sizeof(uint64_t)));
+        GBD_CUDA_TRY(cudaMemcpyAsync(sc.d_long_rows, long_rows.data(), sc.nlong * sizeof(uint32_t),
                                      cudaMemcpyHostToDevice, st));
+        GBD_CUDA_TRY(cudaMemcpyAsync(sc.d_long_prefix, long_prefix.data(),
+                                     (sc.nlong + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
     }
     int rc = build_plan(entries, rows, sc.plan, true, st);
     if (rc != GBD_OK) return rc;
     GBD_CUDA_TRY(cudaStreamSynchronize(st));
+    sc.long_units = long_prefix.back();
     sc.built = true;
     return GBD_OK;
+}
+
+// Rows of the triangle whose read is too long to be a systolic query.
+static int long_rows_general(gbd_ctx *ctx, const gbd_set *set, uint16_t *d_tri, cudaStream_t st)
+{
+    const TriSchedule &sc = set->sched;
+    if (sc.nlong == 0 || sc.long_units == 0) return GBD_OK;
+    GeneralJob gj{set->view(), set->view(), 0, set->n, 0, set->n, 0, OUT_TRI_ROWS, d_tri};
+    gj.rows = sc.d_long_rows;
+    gj.nrows = sc.nlong;
+    gj.row_prefix = sc.d_long_prefix;
+    gj.units_total = sc.long_units;
+    return run_general(gj, scoring_of(ctx), ctx->sm_count, st);
 }
 
 // Copies a host array into stream-ordered device memory freed by the caller.
@@ -109,7 +124,7 @@ static int all_pairs_systolic(gbd_ctx *ctx, gbd_set *set, uint16_t *d_tri, cudaS
     const TriSchedule &sc = set->sched;
     SysJob job{};
     job.Q = job.S = set->view();
-    job.sub_perm = sc.d_perm;
+    job.sub_perm = nullptr;
     job.out = d_tri;
     job.n = set->n;
     job.mode = OUT_TRI;
@@ -119,13 +134,7 @@ static int all_pairs_systolic(gbd_ctx *ctx, gbd_set *set, uint16_t *d_tri, cudaS
     rc = run_systolic(d_job, sc.plan, ctx->sm_count, st);
     cudaFreeAsync(d_job, st);
     if (rc != GBD_OK) return rc;
-    if (sc.long_begin + 1 < set->n) {
-        GeneralJob gj{set->view(), set->view(), 0, set->n, 0, set->n, 0, OUT_TRI_PERM, d_tri};
-        gj.perm = sc.d_perm;
-        gj.p0 = sc.long_begin;
-        rc = run_general(gj, scoring_of(ctx), ctx->sm_count, st);
-    }
-    return rc;
+    return long_rows_general(ctx, set, d_tri, st);
 }
 
 }  // namespace gbd
@@ -289,7 +298,8 @@ void gbd_free_set(gbd_set *set)
     cudaSetDevice(set->device);
     if (set->d_words) cudaFree(set->d_words);
     if (set->d_len) cudaFree(set->d_len);
-    if (set->sched.d_perm) cudaFree(set->sched.d_perm);
+    if (set->sched.d_long_rows) cudaFree(set->sched.d_long_rows);
+    if (set->sched.d_long_prefix) cudaFree(set->sched.d_long_prefix);
     gbd::free_plan(set->sched.plan, nullptr);
     delete set;
 }
@@ -405,17 +415,16 @@ int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns, uint16_t
         SysJob &job = jobs[s];
         job = SysJob{};
         job.Q = job.S = set->view();
-        job.sub_perm = set->sched.d_perm;
+        job.sub_perm = nullptr;
         job.out = d_tris[s];
         job.n = set->n;
         job.mode = OUT_TRI;
         job.conversion = ctx->params.conversion;
         const uint64_t n = set->n;
-        const uint64_t last = std::min<uint64_t>(set->sched.long_begin, n > 0 ? n - 1 : 0);
-        for (uint64_t a = 0; a < last; ++a) {
-            const uint32_t q = set->sched.h_perm[a];
-            entries.push_back({(uint32_t)s, q, (uint32_t)(a + 1), (uint32_t)(n - 1 - a)});
-            rows.push_back((uint8_t)systolic_rows(set->h_len[q]));
+        for (uint64_t i = 0; i + 1 < n; ++i) {
+            if (set->h_len[i] > kSystolicMaxQuery) continue;
+            entries.push_back({(uint32_t)s, (uint32_t)i, (uint32_t)(i + 1), (uint32_t)(n - 1 - i)});
+            rows.push_back((uint8_t)systolic_rows(set->h_len[i]));
         }
     }
     {
@@ -441,14 +450,8 @@ int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns, uint16_t
         if (rc != GBD_OK) return rc;
     }
     for (uint64_t s = 0; s < ns; ++s) {
-        const gbd_set *set = samples[s];
-        if (set->sched.long_begin + 1 < set->n) {
-            GeneralJob gj{set->view(), set->view(), 0, set->n, 0, set->n, 0, OUT_TRI_PERM, d_tris[s]};
-            gj.perm = set->sched.d_perm;
-            gj.p0 = set->sched.long_begin;
-            rc = run_general(gj, scoring_of(ctx), ctx->sm_count, st);
-            if (rc != GBD_OK) return rc;
-        }
+        rc = long_rows_general(ctx, samples[s], d_tris[s], st);
+        if (rc != GBD_OK) return rc;
     }
     return GBD_OK;
 }

@@ -55,15 +55,17 @@ struct SysPlan {
     }
 };
 
-// Device-resident schedule of a read set for the all-pairs triangle: the set's reads in
-// ascending length order, and one systolic entry per read short enough to be a systolic
-// query (query = sorted position a, subjects = sorted positions a+1 .. n-1).
+// Device-resident schedule of a read set for the all-pairs triangle: one systolic entry
+// per read i short enough to be a systolic query (subjects i+1 .. n-1, in the set's own
+// order, so a warp writes a contiguous run of triangle row i), and the list of the
+// longer reads, whose rows go to the general kernel.
 struct TriSchedule {
     bool built = false;
-    std::vector<uint32_t> h_perm;
-    uint32_t *d_perm = nullptr;
     SysPlan plan;                     // entries with job index 0
-    uint64_t long_begin = 0;          // sorted position of the first read longer than 512
+    uint32_t *d_long_rows = nullptr;  // reads longer than the systolic query limit
+    uint64_t *d_long_prefix = nullptr;
+    uint64_t nlong = 0;
+    uint64_t long_units = 0;          // pairs in those rows
 };
 
 }  // namespace gbd
@@ -100,9 +102,9 @@ cudaError_t launch_pack(const uint8_t *seq, const uint64_t *offsets, uint64_t n,
 // Output addressing of a block of pairs.
 //  OUT_TRI:      A == B, pairs i < j, out[k(i,j)] (row-major strict upper triangle)
 //  OUT_RECT:     out[(i-a0)*ld + (j-b0)]
-//  OUT_TRI_PERM: A == B, pairs (perm[p0+x], perm[p0+y]) for 0 <= x < y < n-p0, written at
-//                the triangle index of the two original indices
-enum OutMode : int { OUT_TRI = 0, OUT_RECT = 1, OUT_TRI_PERM = 2 };
+//  OUT_TRI_ROWS: A == B, the triangle rows listed in rows[]: pairs (rows[x], j) for
+//                rows[x] < j < n, units counted by row_prefix (nrows + 1 entries)
+enum OutMode : int { OUT_TRI = 0, OUT_RECT = 1, OUT_TRI_ROWS = 2 };
 
 struct Scoring {
     int match, mismatch, gap, conversion;
@@ -114,10 +116,10 @@ struct GeneralJob {
     uint64_t a0, a1, b0, b1, ld;
     int mode;
     uint16_t *out;
-    const uint32_t *perm = nullptr;   // OUT_TRI_PERM: sorted order of the set
-    uint64_t p0 = 0;                  // OUT_TRI_PERM: first position of the sub-triangle
-    const uint32_t *rows = nullptr;   // OUT_RECT: optional explicit list of A rows
+    const uint32_t *rows = nullptr;   // OUT_RECT / OUT_TRI_ROWS: explicit list of A rows
     uint64_t nrows = 0;
+    const uint64_t *row_prefix = nullptr;   // OUT_TRI_ROWS: pairs before each listed row
+    uint64_t units_total = 0;               // OUT_TRI_ROWS: row_prefix[nrows]
 };
 int run_general(const GeneralJob &job, const Scoring &sc, int sm_count, cudaStream_t stream);
 // Same kernel on a rectangle job, with boundary rows in caller-provided scratch

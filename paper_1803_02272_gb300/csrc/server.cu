@@ -2,18 +2,20 @@
 // rectangular form of `disseq` in section 2.2, used to place new reads into the map of
 // a sample, and the read-vs-reference-database distances of the supervised annotation).
 //
-// Continuous batching:
+// Continuous batching with shortest-remaining-work-first dispatch:
 //  * gbd_server_submit validates and copies a request on the host and queues it; it
 //    returns at once with a ticket (or EBUDGET if the request can never fit).
 //  * A worker thread admits queued requests in arrival order while their footprint (the
-//    output rows plus the packed queries and the work plan) fits the HBM budget beside
-//    the requests in flight.  Everything admitted in one round becomes one batch: the
-//    queries of all its requests are packed on the device and scheduled as one plan --
-//    one launch of the systolic kernel per rows-per-lane bucket -- with one job per
-//    request, so each request's rows go to its own output buffer.
-//  * Batches rotate over four compute streams, so a batch admitted while others are
-//    running starts on the SMs they free.  A host callback at the end
-//    of a batch's stream work marks its requests done and returns their budget.
+//    output rows plus the packed queries) fits the HBM budget beside the requests in
+//    flight.  An admitted request's queries are copied and packed on the device once
+//    (ingest stream), and the request is cut into chunks of about kChunkPairs pairs.
+//  * At most kSlots chunk batches are on the GPU at a time.  Whenever a slot frees, the
+//    worker fills the next batch with chunks of the admitted requests with the least
+//    remaining work first, up to kChunkPairs pairs, and launches it (one launch of the
+//    systolic kernel per rows-per-lane bucket) on the slot's stream, so batches overlap
+//    and a small request never waits behind more than one batch of a large one.
+//  * A host callback at the end of a batch's stream work counts its chunks done; the
+//    last chunk of a request marks it done and returns its budget.
 // Every pair is computed independently by the same kernels whatever else is in the
 // batch, so a request's rows are identical alone and in any mix.
 #include <algorithm>
@@ -32,7 +34,10 @@
 namespace gbd {
 namespace {
 
-enum ReqState { REQ_QUEUED = 0, REQ_RUNNING = 1, REQ_DONE = 2, REQ_FAILED = 3 };
+enum ReqState { REQ_QUEUED = 0, REQ_ACTIVE = 1, REQ_DONE = 2, REQ_FAILED = 3 };
+
+constexpr uint64_t kChunkPairs = 12u << 20;   // ~0.15 s of GPU work per batch
+constexpr int kSlots = 2;                     // chunk batches in flight
 
 struct Request {
     uint64_t ticket = 0;
@@ -40,16 +45,29 @@ struct Request {
     std::vector<uint64_t> off;
     std::vector<uint16_t> len;
     uint64_t nq = 0;
-    uint32_t max_len = 0;
+    uint32_t max_len = 0, stride = 1;
     uint16_t *d_rows = nullptr;
     uint64_t footprint = 0;
     int state = REQ_QUEUED;
     std::string error;
+    // device side, once admitted
+    std::vector<void *> dev;         // allocations to free after the last chunk
+    uint32_t *d_words = nullptr;
+    uint16_t *d_len = nullptr;
+    cudaEvent_t packed = nullptr;
+    uint64_t next_query = 0;         // first query not yet dispatched
+    uint64_t chunks_inflight = 0;
+};
+
+struct Piece {
+    Request *req;
+    uint64_t q0, q1;                 // query range of the request
 };
 
 struct Batch {
-    std::vector<Request *> reqs;
+    std::vector<Piece> pieces;
     struct gbd_server *srv = nullptr;
+    int slot = 0;
 };
 
 }  // namespace
@@ -60,16 +78,17 @@ using namespace gbd;
 struct gbd_server {
     gbd_ctx *ctx = nullptr;
     const gbd_set *ref = nullptr;
-    static constexpr int kStreams = 4;
-    cudaStream_t streams[kStreams] = {};
-    int next_stream = 0;
+    cudaStream_t slots[kSlots] = {};
+    bool slot_busy[kSlots] = {};
+    cudaStream_t ingest = nullptr;
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<Request *> queue;
+    std::deque<Request *> queue;               // submitted, not admitted
+    std::vector<Request *> active;             // admitted, not finished
+    std::vector<std::vector<void *>> garbage;  // device memory of finished requests
     std::unordered_map<uint64_t, std::unique_ptr<Request>> table;
     uint64_t budget = 0, used = 0, next_ticket = 1;
-    int inflight = 0;
     bool stop = false;
 };
 
@@ -82,69 +101,87 @@ bool valid_base(uint8_t c)
     return u == 'a' || u == 'c' || u == 'g' || u == 't';
 }
 
+bool use_systolic_scores(const gbd_params &p)
+{
+    return p.kernel != GBD_KERNEL_GENERAL && p.match == 1 && p.mismatch == -1 && p.gap == 1;
+}
+
+// Called with srv->mu held: one chunk of r finished (or failed with `err`).
+void chunk_finished(gbd_server *srv, Request *r, const std::string &err)
+{
+    if (!err.empty() && r->error.empty()) r->error = err;
+    --r->chunks_inflight;
+    if (r->chunks_inflight == 0 && (r->next_query >= r->nq || !r->error.empty())) {
+        r->state = r->error.empty() ? REQ_DONE : REQ_FAILED;
+        r->next_query = r->nq;
+        srv->used -= r->footprint;
+        srv->garbage.push_back(std::move(r->dev));
+        r->dev.clear();
+        srv->active.erase(std::remove(srv->active.begin(), srv->active.end(), r), srv->active.end());
+    }
+}
+
 void CUDART_CB batch_done(void *arg)
 {
-    // Runs on a CUDA callback thread once the batch's work on its stream has finished:
-    // no CUDA calls here, only bookkeeping.
+    // Runs on a CUDA callback thread once the batch's stream work has finished: no CUDA
+    // calls here, only bookkeeping.
     Batch *b = static_cast<Batch *>(arg);
     gbd_server *srv = b->srv;
     {
         std::lock_guard<std::mutex> lk(srv->mu);
-        for (Request *r : b->reqs) {
-            r->state = r->error.empty() ? REQ_DONE : REQ_FAILED;
-            srv->used -= r->footprint;
-        }
-        --srv->inflight;
+        for (const Piece &p : b->pieces) chunk_finished(srv, p.req, std::string());
+        srv->slot_busy[b->slot] = false;
     }
     srv->cv_done.notify_all();
     srv->cv_work.notify_all();
     delete b;
 }
 
-// Packs every query of the batch and launches its plan on `st`; returns a message on
-// failure (the requests are then failed).
-std::string launch_batch(gbd_server *srv, const std::vector<Request *> &reqs, cudaStream_t st)
+// Copies and packs an admitted request's queries on the ingest stream.
+std::string admit(gbd_server *srv, Request *r)
 {
-    gbd_ctx *ctx = srv->ctx;
-    const gbd_set *ref = srv->ref;
-    const size_t nr = reqs.size();
-    std::vector<SysJob> jobs(nr);
-    std::vector<SysEntry> entries;
-    std::vector<uint8_t> rows;
-    std::vector<void *> to_free;
+    cudaStream_t st = srv->ingest;
     std::string err;
     auto cu = [&](cudaError_t e, const char *what) {
         if (e != cudaSuccess && err.empty()) err = std::string(what) + ": " + cudaGetErrorString(e);
         return e == cudaSuccess;
     };
+    uint8_t *d_seq = nullptr;
+    uint64_t *d_off = nullptr;
+    unsigned long long *d_err = nullptr;
+    const size_t nbytes = std::max<size_t>(r->seq.size(), 1);
+    if (cu(cudaMallocAsync((void **)&d_seq, nbytes, st), "cudaMallocAsync")) r->dev.push_back(d_seq);
+    if (cu(cudaMallocAsync((void **)&d_off, (r->nq + 1) * 8, st), "cudaMallocAsync")) r->dev.push_back(d_off);
+    if (cu(cudaMallocAsync((void **)&r->d_words, r->nq * r->stride * 4, st), "cudaMallocAsync"))
+        r->dev.push_back(r->d_words);
+    if (cu(cudaMallocAsync((void **)&r->d_len, r->nq * 2, st), "cudaMallocAsync")) r->dev.push_back(r->d_len);
+    if (cu(cudaMallocAsync((void **)&d_err, 8, st), "cudaMallocAsync")) r->dev.push_back(d_err);
+    if (!err.empty()) return err;
+    if (!r->seq.empty()) cu(cudaMemcpyAsync(d_seq, r->seq.data(), r->seq.size(), cudaMemcpyHostToDevice, st), "H2D");
+    cu(cudaMemcpyAsync(d_off, r->off.data(), (r->nq + 1) * 8, cudaMemcpyHostToDevice, st), "H2D");
+    if (err.empty()) cu(launch_pack(d_seq, d_off, r->nq, r->stride, r->d_words, r->d_len, d_err, st), "pack");
+    if (err.empty() && cu(cudaEventCreateWithFlags(&r->packed, cudaEventDisableTiming), "cudaEventCreate"))
+        cu(cudaEventRecord(r->packed, st), "cudaEventRecord");
+    return err;
+}
+
+// Launches one batch of pieces on stream st; returns an error message or "".
+std::string launch_batch(gbd_server *srv, const std::vector<Piece> &pieces, cudaStream_t st)
+{
+    gbd_ctx *ctx = srv->ctx;
+    const gbd_set *ref = srv->ref;
+    const bool systolic = use_systolic_scores(ctx->params);
+    std::vector<SysJob> jobs;
+    std::vector<SysEntry> entries;
+    std::vector<uint8_t> rows;
+    std::vector<void *> to_free;
+    std::string err;
     uint64_t total_pairs = 0;
-    for (size_t k = 0; k < nr && err.empty(); ++k) {
-        Request *r = reqs[k];
-        const uint32_t stride = std::max<uint32_t>(1, (r->max_len + kBasesPerWord - 1) / kBasesPerWord);
-        uint8_t *d_seq = nullptr;
-        uint64_t *d_off = nullptr;
-        uint32_t *d_words = nullptr;
-        uint16_t *d_len = nullptr;
-        unsigned long long *d_err = nullptr;
-        const size_t nbytes = std::max<size_t>(r->seq.size(), 1);
-        if (!cu(cudaMallocAsync((void **)&d_seq, nbytes, st), "cudaMallocAsync")) break;
-        to_free.push_back(d_seq);
-        if (!cu(cudaMallocAsync((void **)&d_off, (r->nq + 1) * 8, st), "cudaMallocAsync")) break;
-        to_free.push_back(d_off);
-        if (!cu(cudaMallocAsync((void **)&d_words, r->nq * stride * 4, st), "cudaMallocAsync")) break;
-        to_free.push_back(d_words);
-        if (!cu(cudaMallocAsync((void **)&d_len, r->nq * 2, st), "cudaMallocAsync")) break;
-        to_free.push_back(d_len);
-        if (!cu(cudaMallocAsync((void **)&d_err, 8, st), "cudaMallocAsync")) break;
-        to_free.push_back(d_err);
-        if (!r->seq.empty() &&
-            !cu(cudaMemcpyAsync(d_seq, r->seq.data(), r->seq.size(), cudaMemcpyHostToDevice, st), "H2D"))
-            break;
-        if (!cu(cudaMemcpyAsync(d_off, r->off.data(), (r->nq + 1) * 8, cudaMemcpyHostToDevice, st), "H2D")) break;
-        if (!cu(launch_pack(d_seq, d_off, r->nq, stride, d_words, d_len, d_err, st), "pack")) break;
-        SysJob &J = jobs[k];
-        J = SysJob{};
-        J.Q = {d_words, d_len, r->nq, stride};
+    for (const Piece &p : pieces) {
+        Request *r = p.req;
+        if (r->packed && cudaStreamWaitEvent(st, r->packed, 0) != cudaSuccess) return "cudaStreamWaitEvent failed";
+        SysJob J{};
+        J.Q = {r->d_words, r->d_len, r->nq, r->stride};
         J.S = ref->view();
         J.sub_perm = nullptr;
         J.out = r->d_rows;
@@ -153,52 +190,80 @@ std::string launch_batch(gbd_server *srv, const std::vector<Request *> &reqs, cu
         J.col0 = 0;
         J.mode = OUT_RECT;
         J.conversion = ctx->params.conversion;
+        const uint32_t job = (uint32_t)jobs.size();
+        jobs.push_back(J);
         std::vector<uint32_t> long_rows;
-        const gbd_params &pp = ctx->params;
-        const bool systolic = pp.kernel != GBD_KERNEL_GENERAL && pp.match == 1 && pp.mismatch == -1 &&
-                              pp.gap == 1;
-        for (uint64_t i = 0; i < r->nq; ++i) {
+        for (uint64_t i = p.q0; i < p.q1; ++i) {
             if (systolic && r->len[i] <= kSystolicMaxQuery) {
-                entries.push_back({(uint32_t)k, (uint32_t)i, 0u, (uint32_t)ref->n});
+                entries.push_back({job, (uint32_t)i, 0u, (uint32_t)ref->n});
                 rows.push_back((uint8_t)systolic_rows(r->len[i]));
             } else {
                 long_rows.push_back((uint32_t)i);
             }
         }
-        total_pairs += r->nq * ref->n;
+        total_pairs += (p.q1 - p.q0) * ref->n;
         if (!long_rows.empty()) {
-            uint32_t *d_rows_list = nullptr;
-            if (!cu(cudaMallocAsync((void **)&d_rows_list, long_rows.size() * 4, st), "cudaMallocAsync")) break;
-            to_free.push_back(d_rows_list);
-            if (!cu(cudaMemcpyAsync(d_rows_list, long_rows.data(), long_rows.size() * 4,
-                                    cudaMemcpyHostToDevice, st), "H2D"))
-                break;
+            uint32_t *d_list = nullptr;
+            if (cudaMallocAsync((void **)&d_list, long_rows.size() * 4, st) != cudaSuccess) return "cudaMallocAsync failed";
+            to_free.push_back(d_list);
+            if (cudaMemcpyAsync(d_list, long_rows.data(), long_rows.size() * 4, cudaMemcpyHostToDevice, st) !=
+                cudaSuccess)
+                return "H2D failed";
             GeneralJob gj{J.Q, J.S, 0, r->nq, 0, ref->n, ref->n, OUT_RECT, r->d_rows};
-            gj.rows = d_rows_list;
+            gj.rows = d_list;
             gj.nrows = long_rows.size();
             const Scoring sc{ctx->params.match, ctx->params.mismatch, ctx->params.gap, ctx->params.conversion};
             if (run_general(gj, sc, ctx->sm_count, st) != GBD_OK) err = gbd_last_error();
         }
     }
     if (err.empty() && !entries.empty()) {
-        // small batches: shorter pieces so the batch still spreads over every SM
+        // short pieces of subjects so that even a one-query batch covers every SM
         const uint64_t warps = (uint64_t)systolic_resident_warps(ctx->sm_count);
         uint64_t piece = total_pairs / std::max<uint64_t>(1, 4 * warps);
         piece = std::min<uint64_t>(kSystolicPiece, std::max<uint64_t>(64, piece));
         SysJob *d_jobs = nullptr;
-        if (cu(cudaMallocAsync((void **)&d_jobs, nr * sizeof(SysJob), st), "cudaMallocAsync")) {
+        if (cudaMallocAsync((void **)&d_jobs, jobs.size() * sizeof(SysJob), st) == cudaSuccess) {
             to_free.push_back(d_jobs);
-            if (cu(cudaMemcpyAsync(d_jobs, jobs.data(), nr * sizeof(SysJob), cudaMemcpyHostToDevice, st), "H2D")) {
+            if (cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(SysJob), cudaMemcpyHostToDevice, st) ==
+                cudaSuccess) {
                 SysPlan plan;
                 if (build_plan(entries, rows, plan, false, st, (uint32_t)piece) != GBD_OK ||
                     run_systolic(d_jobs, plan, ctx->sm_count, st) != GBD_OK)
                     err = gbd_last_error();
                 free_plan(plan, st);
+            } else {
+                err = "H2D failed";
             }
+        } else {
+            err = "cudaMallocAsync failed";
         }
     }
     for (void *p : to_free) cudaFreeAsync(p, st);
     return err;
+}
+
+// Next batch: chunks of the admitted requests, least remaining work first.
+std::vector<Piece> next_pieces(gbd_server *srv)
+{
+    std::vector<Request *> cand;
+    for (Request *r : srv->active)
+        if (r->next_query < r->nq && r->error.empty()) cand.push_back(r);
+    std::sort(cand.begin(), cand.end(), [](const Request *a, const Request *b) {
+        return (a->nq - a->next_query) < (b->nq - b->next_query) ||
+               ((a->nq - a->next_query) == (b->nq - b->next_query) && a->ticket < b->ticket);
+    });
+    std::vector<Piece> out;
+    const uint64_t n_ref = srv->ref->n;
+    uint64_t room = std::max<uint64_t>(kChunkPairs / n_ref, 1);   // queries in this batch
+    for (Request *r : cand) {
+        if (room == 0) break;
+        const uint64_t take = std::min<uint64_t>(room, r->nq - r->next_query);
+        out.push_back({r, r->next_query, r->next_query + take});
+        r->next_query += take;
+        ++r->chunks_inflight;
+        room -= take;
+    }
+    return out;
 }
 
 void worker_main(gbd_server *srv)
@@ -206,51 +271,71 @@ void worker_main(gbd_server *srv)
     cudaSetDevice(srv->ctx->device);
     std::unique_lock<std::mutex> lk(srv->mu);
     for (;;) {
+        // free device memory of finished requests (their kernels have completed)
+        if (!srv->garbage.empty()) {
+            std::vector<std::vector<void *>> g;
+            g.swap(srv->garbage);
+            lk.unlock();
+            for (auto &v : g)
+                for (void *p : v) cudaFreeAsync(p, srv->ingest);
+            lk.lock();
+        }
         // admit in arrival order while the budget allows (a request always fits when
-        // nothing else is in flight: submit rejected those that never fit)
-        std::vector<Request *> batch;
+        // nothing else is admitted: submit rejected those that never fit)
+        bool progressed = false;
         while (!srv->queue.empty()) {
             Request *r = srv->queue.front();
-            if (srv->used + r->footprint > srv->budget && (srv->used > 0 || !batch.empty())) break;
+            if (srv->used + r->footprint > srv->budget && srv->used > 0) break;
             srv->queue.pop_front();
             srv->used += r->footprint;
-            r->state = REQ_RUNNING;
-            batch.push_back(r);
-        }
-        if (!batch.empty()) {
-            const int si = srv->next_stream;
-            srv->next_stream = (si + 1) % gbd_server::kStreams;
-            ++srv->inflight;
+            r->state = REQ_ACTIVE;
+            srv->active.push_back(r);
             lk.unlock();
-            cudaStream_t st = srv->streams[si];
+            std::string err = admit(srv, r);
+            lk.lock();
+            if (!err.empty()) {
+                r->error = err;
+                ++r->chunks_inflight;
+                chunk_finished(srv, r, err);
+                srv->cv_done.notify_all();
+            }
+            progressed = true;
+        }
+        // dispatch into every free slot
+        for (int s = 0; s < kSlots; ++s) {
+            if (srv->slot_busy[s]) continue;
+            std::vector<Piece> pieces = next_pieces(srv);
+            if (pieces.empty()) break;
+            srv->slot_busy[s] = true;
+            lk.unlock();
+            cudaStream_t st = srv->slots[s];
             std::string err;
             try {
-                err = launch_batch(srv, batch, st);
+                err = launch_batch(srv, pieces, st);
             } catch (const std::exception &e) {
                 err = std::string("server batch: ") + e.what();
             }
-            Batch *b = new Batch{batch, srv};
-            if (!err.empty()) {
-                // published as failed by batch_done, after the stream work has drained
-                lk.lock();
-                for (Request *r : batch) r->error = err;
-                lk.unlock();
-            }
-            cudaError_t e = cudaLaunchHostFunc(st, batch_done, b);
+            Batch *b = new Batch{pieces, srv, s};
+            cudaError_t e = cudaSuccess;
+            if (err.empty()) e = cudaLaunchHostFunc(st, batch_done, b);
             lk.lock();
-            if (e != cudaSuccess) {
-                for (Request *r : batch) {
-                    r->state = REQ_FAILED;
-                    if (r->error.empty()) r->error = cudaGetErrorString(e);
-                    srv->used -= r->footprint;
-                }
-                --srv->inflight;
+            if (!err.empty() || e != cudaSuccess) {
+                // launch failed: drain the stream before releasing the pieces
+                lk.unlock();
+                cudaStreamSynchronize(st);
+                lk.lock();
+                const std::string msg = err.empty() ? std::string(cudaGetErrorString(e)) : err;
+                for (const Piece &p : pieces) chunk_finished(srv, p.req, msg);
+                srv->slot_busy[s] = false;
                 delete b;
                 srv->cv_done.notify_all();
             }
-            continue;
+            progressed = true;
         }
-        if (srv->stop && srv->inflight == 0) break;
+        if (progressed) continue;
+        bool busy = false;
+        for (int s = 0; s < kSlots; ++s) busy = busy || srv->slot_busy[s];
+        if (srv->stop && srv->active.empty() && srv->queue.empty() && !busy) break;
         srv->cv_work.wait(lk);
     }
 }
@@ -273,8 +358,8 @@ int gbd_server_create(gbd_ctx *ctx, const gbd_set *ref, gbd_server **out)
     size_t free_b = 0, total_b = 0;
     GBD_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     srv->budget = ctx->params.hbm_budget ? ctx->params.hbm_budget : (uint64_t)(0.9 * (double)free_b);
-    for (int i = 0; i < gbd_server::kStreams; ++i)
-        GBD_CUDA_TRY(cudaStreamCreateWithFlags(&srv->streams[i], cudaStreamNonBlocking));
+    for (int i = 0; i < kSlots; ++i) GBD_CUDA_TRY(cudaStreamCreateWithFlags(&srv->slots[i], cudaStreamNonBlocking));
+    GBD_CUDA_TRY(cudaStreamCreateWithFlags(&srv->ingest, cudaStreamNonBlocking));
     srv->worker = std::thread(worker_main, srv.get());
     *out = srv.release();
     return GBD_OK;
@@ -308,8 +393,8 @@ int gbd_server_submit(gbd_server *srv, const uint8_t *seq, const uint64_t *offse
         if (!valid_base(r->seq[k]))
             return fail(GBD_EINVAL, "gbd_server_submit: byte at position " + std::to_string(k) +
                                         " is not one of A, C, G, T");
-    const uint32_t stride = std::max<uint32_t>(1, (r->max_len + kBasesPerWord - 1) / kBasesPerWord);
-    r->footprint = nq * srv->ref->n * 2 + nbytes + (nq + 1) * 8 + nq * (stride * 4 + 2) + 64 * nq;
+    r->stride = std::max<uint32_t>(1, (r->max_len + kBasesPerWord - 1) / kBasesPerWord);
+    r->footprint = nq * srv->ref->n * 2 + nbytes + (nq + 1) * 8 + nq * (r->stride * 4 + 2) + 64 * nq;
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         if (r->footprint > srv->budget)
@@ -324,7 +409,7 @@ int gbd_server_submit(gbd_server *srv, const uint8_t *seq, const uint64_t *offse
     return GBD_OK;
 }
 
-static int report(gbd_server *srv, std::unique_lock<std::mutex> &lk, uint64_t ticket, int *done)
+static int report(gbd_server *srv, uint64_t ticket, int *done)
 {
     auto it = srv->table.find(ticket);
     if (it == srv->table.end()) return fail(GBD_ENOTFOUND, "gbd_server: unknown ticket " + std::to_string(ticket));
@@ -332,21 +417,21 @@ static int report(gbd_server *srv, std::unique_lock<std::mutex> &lk, uint64_t ti
     if (r->state == REQ_DONE || r->state == REQ_FAILED) {
         const bool ok = r->state == REQ_DONE;
         const std::string msg = r->error;
+        if (r->packed) cudaEventDestroy(r->packed);
         srv->table.erase(it);                       // a finished ticket is reported once
         if (done) *done = 1;
         if (!ok) return fail(GBD_ECUDA, "gbd_server request failed: " + msg);
         return GBD_OK;
     }
     if (done) *done = 0;
-    (void)lk;
     return GBD_OK;
 }
 
 int gbd_server_poll(gbd_server *srv, uint64_t ticket, int *done)
 {
     if (!srv || !done) return fail(GBD_EINVAL, "gbd_server_poll: NULL argument");
-    std::unique_lock<std::mutex> lk(srv->mu);
-    return report(srv, lk, ticket, done);
+    std::lock_guard<std::mutex> lk(srv->mu);
+    return report(srv, ticket, done);
 }
 
 int gbd_server_wait(gbd_server *srv, uint64_t ticket)
@@ -359,11 +444,11 @@ int gbd_server_wait(gbd_server *srv, uint64_t ticket)
         auto it = srv->table.find(ticket);
         if (it == srv->table.end()) return fail(GBD_ENOTFOUND, "gbd_server_wait: unknown ticket " + std::to_string(ticket));
         const int st = it->second->state;
-        if (st == REQ_DONE || st == REQ_FAILED) return report(srv, lk, ticket, nullptr);
+        if (st == REQ_DONE || st == REQ_FAILED) return report(srv, ticket, nullptr);
         if (srv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
             auto it2 = srv->table.find(ticket);
             if (it2 != srv->table.end() && (it2->second->state == REQ_DONE || it2->second->state == REQ_FAILED))
-                return report(srv, lk, ticket, nullptr);
+                return report(srv, ticket, nullptr);
             return fail(GBD_ETIMEDOUT, "gbd_server_wait: ticket " + std::to_string(ticket) + " not done after " +
                                            std::to_string(tmo) + " us");
         }
@@ -380,11 +465,19 @@ void gbd_server_destroy(gbd_server *srv)
     srv->cv_work.notify_all();
     if (srv->worker.joinable()) srv->worker.join();
     cudaSetDevice(srv->ctx->device);
-    for (int i = 0; i < gbd_server::kStreams; ++i) {
-        if (srv->streams[i]) {
-            cudaStreamSynchronize(srv->streams[i]);
-            cudaStreamDestroy(srv->streams[i]);
+    for (auto &v : srv->garbage)
+        for (void *p : v) cudaFreeAsync(p, srv->ingest);
+    for (auto &kv : srv->table)
+        if (kv.second->packed) cudaEventDestroy(kv.second->packed);
+    for (int i = 0; i < kSlots; ++i) {
+        if (srv->slots[i]) {
+            cudaStreamSynchronize(srv->slots[i]);
+            cudaStreamDestroy(srv->slots[i]);
         }
+    }
+    if (srv->ingest) {
+        cudaStreamSynchronize(srv->ingest);
+        cudaStreamDestroy(srv->ingest);
     }
     delete srv;
 }

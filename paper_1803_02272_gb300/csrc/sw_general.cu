@@ -66,12 +66,14 @@ sw_general_kernel(GeneralJob job, Scoring sc, int *__restrict__ scratch, uint64_
             uint64_t ti, tj;
             tri_unindex(u, job.A.n, ti, tj);
             ia = ti; jb = tj; o = u;
-        } else if (job.mode == OUT_TRI_PERM) {
-            uint64_t x, y;
-            tri_unindex(u, job.A.n - job.p0, x, y);
-            const uint64_t pa = job.perm[job.p0 + x], pb = job.perm[job.p0 + y];
-            ia = pa < pb ? pa : pb;
-            jb = pa < pb ? pb : pa;
+        } else if (job.mode == OUT_TRI_ROWS) {
+            uint64_t lo = 0, hi = job.nrows;           // row_prefix[lo] <= u < row_prefix[lo+1]
+            while (hi - lo > 1) {
+                const uint64_t mid = (lo + hi) >> 1;
+                if (job.row_prefix[mid] <= u) lo = mid; else hi = mid;
+            }
+            ia = job.rows[lo];
+            jb = ia + 1 + (u - job.row_prefix[lo]);
             o = ia * job.A.n - ia * (ia + 1) / 2 + (jb - ia - 1);
         } else {
             const uint64_t r = u / nb;
@@ -123,9 +125,8 @@ int run_general(const GeneralJob &job, const Scoring &sc, int sm_count, cudaStre
     if (job.mode == OUT_TRI) {
         const uint64_t n = job.A.n;
         units = n < 2 ? 0 : n * (n - 1) / 2;
-    } else if (job.mode == OUT_TRI_PERM) {
-        const uint64_t m = job.A.n - job.p0;
-        units = m < 2 ? 0 : m * (m - 1) / 2;
+    } else if (job.mode == OUT_TRI_ROWS) {
+        units = job.units_total;
     } else {
         units = (job.rows ? job.nrows : (job.a1 - job.a0)) * (job.b1 - job.b0);
     }

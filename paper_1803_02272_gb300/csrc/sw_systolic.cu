@@ -7,8 +7,8 @@
 // Layout of the work (one warp = one work unit = one query vs many subjects):
 //  * Lane k owns query rows [kR, kR+R) (R = ceil(la/32) <= 16).  Subjects flow through
 //    the warp as a stream of columns; lane k runs 16 steps behind lane k-1, so the value
-//    of lane k-1's last row reaches lane k by a warp shuffle (plus a (16-R)-step delay
-//    line when R < 16).  The two 16-bit halves of every register carry two independent
+//    of lane k-1's last row reaches lane k by a warp shuffle, 16-R steps late when R < 16
+//    (the sending row keeps its last 16 outputs in registers).  The two 16-bit halves of every register carry two independent
 //    subject streams (int16x2 SIMD).
 //  * Within a lane, row r at local step u handles stream column u - r, so the R cells a
 //    lane updates per step lie on one anti-diagonal and are independent.
@@ -250,10 +250,14 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
     uint32_t V0[R], V1[R];                     // V0: even local steps, V1: odd
 #pragma unroll
     for (int r = 0; r < R; ++r) { V1[r] = f_prev; V0[r] = f_prev2; }
-    uint32_t fifo[D > 0 ? D : 1];
+    // Row R-1 of lane k reaches lane k+1 after 1 + D steps.  With D > 0 the row keeps its
+    // outputs of the last 16 steps in hist[step in chunk] (static register names, no
+    // copies) and the next lane shuffles the entry it needs directly; with D == 0 the
+    // row lives in V0/V1 like the others.
+    constexpr bool HIST = D > 0;
+    uint32_t hist[HIST ? CH : 1];
 #pragma unroll
-    for (int i = 0; i < (D > 0 ? D : 1); ++i) fifo[i] = f_prev;
-    uint32_t sendv = f_prev;                   // row R-1 value offered to the next lane
+    for (int i = 0; i < (HIST ? CH : 1); ++i) hist[i] = f_prev;
     uint32_t up0_prev = f_prev2;               // row 0's diagonal input
     uint32_t curRel = 0, prevRel = 0, acc = 0, emit = 0;
     uint32_t Mlast_prev = 0;                   // "ends a subject" masks of chunk c-1
@@ -284,8 +288,8 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
 #pragma unroll
             for (int r = 0; r < R; ++r) { V0[r] -= REBASE2; V1[r] -= REBASE2; }
 #pragma unroll
-            for (int i = 0; i < (D > 0 ? D : 1); ++i) fifo[i] -= REBASE2;
-            sendv -= REBASE2; up0_prev -= REBASE2; f_prev -= REBASE2; f_prev2 -= REBASE2;
+            for (int i = 0; i < (HIST ? CH : 1); ++i) hist[i] -= REBASE2;
+            up0_prev -= REBASE2; f_prev -= REBASE2; f_prev2 -= REBASE2;
             prevRel -= REBASE2;               // curRel is 0 (minus infinity) here
         }
 
@@ -308,56 +312,52 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
             uint32_t *cur = (q & 1) ? V0 : V1;        // V(u-1)
             uint32_t *nxt = (q & 1) ? V1 : V0;        // V(u-2) in, V(u) out
             const uint32_t f = f_prev + ONE2;
-            const uint32_t got = __shfl_up_sync(0xffffffffu, sendv, 1);
-            uint32_t up0;
-            if constexpr (D > 0) {
-                up0 = fifo[0];
-#pragma unroll
-                for (int i = 0; i + 1 < D; ++i) fifo[i] = fifo[i + 1];
-                fifo[D - 1] = got;
-            } else {
-                up0 = got;
-            }
+            // row R-1 of lane k-1, produced 1 + D steps ago
+            uint32_t up0 = __shfl_up_sync(0xffffffffu,
+                                          HIST ? hist[(q + CH - 1 - D) & (CH - 1)] : cur[R - 1], 1);
             if (lane == 0) up0 = f_prev;              // top boundary: H(0, j) = 0
             uint32_t diag0 = up0_prev;
 #pragma unroll
             for (int r = R - 1; r >= 0; --r) {
+                // this row's value one step ago (left input) and its new value
+                uint32_t &left = (HIST && r == R - 1) ? hist[(q + CH - 1) & (CH - 1)] : cur[r];
+                uint32_t &out = (HIST && r == R - 1) ? hist[q] : nxt[r];
                 if (r == q) {
                     // row q reaches a subject's first column: its left input (and, for
                     // row 0, its diagonal) become the floor of column 0.  Rows below
                     // already read the old value as their "up" input this step.
-                    cur[r] = lop_sel(cur[r], f_prev, Mfirst);
+                    left = lop_sel(left, f_prev, Mfirst);
                     if (r == 0) diag0 = lop_sel(diag0, f_prev2, Mfirst);
                 }
                 const uint32_t up = r ? cur[r - 1] : up0;
                 const uint32_t dg = r ? nxt[r - 1] : diag0;
                 const uint32_t s2 = (((q - r) & 1) == 0) ? sp[r].x : sp[r].y;
                 const uint32_t E = vaddmax(dg, s2, f);
-                nxt[r] = vmax3(up, cur[r], E);
+                out = vmax3(up, left, E);
                 if (((q - r) & 1) != 0) sp[r] = lds64(ws, addr[r] + 4 * poff(q + 1 - r));
             }
-            sendv = nxt[R - 1];
             up0_prev = up0;
             // best: rows <= q are in column chunk c, rows > q in chunk c-1
             {
                 const int nN = (q < R - 1 ? q : R - 1) + 1;
-                uint32_t mN = nxt[0];
+                auto val = [&](int r) -> uint32_t { return (HIST && r == R - 1) ? hist[q] : nxt[r]; };
+                uint32_t mN = val(0);
 #pragma unroll
                 for (int r = 1; r < R; r += 2) {
                     if (r < nN) {
-                        if (r + 1 < nN) mN = vmax3(mN, nxt[r], nxt[r + 1]);
-                        else mN = vmax2(mN, nxt[r]);
+                        if (r + 1 < nN) mN = vmax3(mN, val(r), val(r + 1));
+                        else mN = vmax2(mN, val(r));
                     }
                 }
                 curRel = vaddmax(mN, pack2(-q), curRel);
                 if (nN < R) {
-                    uint32_t mO = nxt[nN];
+                    uint32_t mO = val(nN);
 #pragma unroll
                     for (int r = 1; r < R; r += 2) {
                         const int a = nN + r, b = nN + r + 1;
                         if (a < R) {
-                            if (b < R) mO = vmax3(mO, nxt[a], nxt[b]);
-                            else mO = vmax2(mO, nxt[a]);
+                            if (b < R) mO = vmax3(mO, val(a), val(b));
+                            else mO = vmax2(mO, val(a));
                         }
                     }
                     prevRel = vaddmax(mO, pack2(-q), prevRel);
