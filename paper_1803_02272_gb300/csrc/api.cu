@@ -14,6 +14,7 @@ namespace gbd {
 
 static thread_local std::string t_last_error;
 static std::atomic<uint64_t> g_launches{0};
+static std::atomic<uint64_t> g_set_ids{0};
 
 void note_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
@@ -83,7 +84,7 @@ static int build_tri_schedule(gbd_set *set, cudaStream_t st)
         GBD_CUDA_TRY(cudaMemcpyAsync(sc.d_long_prefix, long_prefix.data(),
                                      (sc.nlong + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
     }
-    int rc = build_plan(entries, rows, sc.plan, true, st);
+    int rc = build_plan(entries, rows, sc.plan, true, st, 0, set->mean_len, set->ctx->sm_count);
     if (rc != GBD_OK) return rc;
     GBD_CUDA_TRY(cudaStreamSynchronize(st));
     sc.long_units = long_prefix.back();
@@ -131,10 +132,109 @@ static int all_pairs_systolic(gbd_ctx *ctx, gbd_set *set, uint16_t *d_tri, cudaS
     job.conversion = ctx->params.conversion;
     SysJob *d_job = nullptr;
     if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
-    rc = run_systolic(d_job, sc.plan, ctx->sm_count, st);
+    rc = run_systolic(d_job, sc.plan, ctx->sm_count, st, ctx->aux, ctx->fork, ctx->join);
     cudaFreeAsync(d_job, st);
     if (rc != GBD_OK) return rc;
     return long_rows_general(ctx, set, d_tri, st);
+}
+
+
+// Last captured batch: its inputs, persistent job table and plan, and the graph.
+struct BatchGraph {
+    std::vector<uint64_t> ids;
+    std::vector<uint16_t *> outs;
+    int conversion = 0;
+    SysJob *d_jobs = nullptr;
+    SysPlan plan;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t kernels = 0;
+    bool matches(const gbd_set *const *samples, uint64_t ns, uint16_t *const *d_tris, int conv) const
+    {
+        if (ids.size() != ns || conversion != conv) return false;
+        for (uint64_t s = 0; s < ns; ++s)
+            if (ids[s] != samples[s]->id || outs[s] != d_tris[s]) return false;
+        return true;
+    }
+};
+
+void free_batch_cache(gbd_ctx *ctx)
+{
+    BatchGraph *bg = static_cast<BatchGraph *>(ctx->batch_cache);
+    if (!bg) return;
+    if (bg->exec) cudaGraphExecDestroy(bg->exec);
+    if (bg->graph) cudaGraphDestroy(bg->graph);
+    if (bg->d_jobs) cudaFree(bg->d_jobs);
+    free_plan(bg->plan, nullptr);
+    delete bg;
+    ctx->batch_cache = nullptr;
+}
+
+// Builds the batch's job table and plan (persistent) and records its launch group on the
+// context's capture stream.
+static int capture_batch(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const *samples, uint64_t ns,
+                         uint16_t *const *d_tris)
+{
+    cudaStream_t cap = ctx->capture;
+    std::vector<SysJob> jobs(ns);
+    std::vector<SysEntry> entries;
+    std::vector<uint8_t> rows;
+    double len_sum = 0.0, n_sum = 0.0;
+    for (uint64_t s = 0; s < ns; ++s) {
+        const gbd_set *set = samples[s];
+        bg->ids.push_back(set->id);
+        bg->outs.push_back(d_tris[s]);
+        SysJob &job = jobs[s];
+        job = SysJob{};
+        job.Q = job.S = set->view();
+        job.sub_perm = nullptr;
+        job.out = d_tris[s];
+        job.n = set->n;
+        job.mode = OUT_TRI;
+        job.conversion = ctx->params.conversion;
+        for (uint64_t i = 0; i + 1 < set->n; ++i) {
+            if (set->h_len[i] > kSystolicMaxQuery) continue;
+            entries.push_back({(uint32_t)s, (uint32_t)i, (uint32_t)(i + 1), (uint32_t)(set->n - 1 - i)});
+            rows.push_back((uint8_t)systolic_rows(set->h_len[i]));
+        }
+        len_sum += set->mean_len * (double)set->n;
+        n_sum += (double)set->n;
+    }
+    bg->conversion = ctx->params.conversion;
+    {
+        std::vector<size_t> order(entries.size());
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](size_t x, size_t y) { return entries[x].nsub > entries[y].nsub; });
+        std::vector<SysEntry> e2(entries.size());
+        std::vector<uint8_t> r2(entries.size());
+        for (size_t i = 0; i < order.size(); ++i) { e2[i] = entries[order[i]]; r2[i] = rows[order[i]]; }
+        entries.swap(e2);
+        rows.swap(r2);
+    }
+    if (ns > 0) {
+        GBD_CUDA_TRY(cudaMalloc((void **)&bg->d_jobs, ns * sizeof(SysJob)));
+        GBD_CUDA_TRY(cudaMemcpy(bg->d_jobs, jobs.data(), ns * sizeof(SysJob), cudaMemcpyHostToDevice));
+    }
+    const double mean_len = n_sum > 0 ? len_sum / n_sum : 0.0;
+    int rc = build_plan(entries, rows, bg->plan, true, cap, 0, mean_len, ctx->sm_count);
+    if (rc != GBD_OK) return rc;
+    const uint64_t launches0 = gbd_kernel_launches();
+    GBD_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    rc = run_systolic(bg->d_jobs, bg->plan, ctx->sm_count, cap, ctx->aux, ctx->fork, ctx->join);
+    for (uint64_t s = 0; s < ns && rc == GBD_OK; ++s) rc = long_rows_general(ctx, samples[s], d_tris[s], cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
+    if (rc != GBD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    bg->graph = g;
+    GBD_CUDA_TRY(cudaGraphInstantiate(&bg->exec, g, 0));
+    // the capture counted the kernels it recorded; every replay runs them again
+    bg->kernels = gbd_kernel_launches() - launches0;
+    return GBD_OK;
 }
 
 }  // namespace gbd
@@ -182,15 +282,33 @@ int gbd_create(gbd_ctx **out, int device, const gbd_params *p)
     ctx->device = device;
     ctx->params = prm;
     cudaError_t e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         delete ctx;
-        return cuda_fail(e, "cudaDeviceGetAttribute");
+        return cuda_fail(e, "gbd_create");
     }
     *out = ctx;
     return GBD_OK;
 }
 
-void gbd_destroy(gbd_ctx *ctx) { delete ctx; }
+void gbd_destroy(gbd_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    free_batch_cache(ctx);
+    for (cudaStream_t st : {ctx->aux, ctx->capture}) {
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
+    }
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->join) cudaEventDestroy(ctx->join);
+    delete ctx;
+}
 
 int gbd_load_reads(gbd_ctx *ctx, const uint8_t *seq, const uint64_t *offsets, uint64_t n,
                    gbd_set **out, void *stream)
@@ -235,6 +353,8 @@ int gbd_load_reads(gbd_ctx *ctx, const uint8_t *seq, const uint64_t *offsets, ui
     set->max_len = max_len;
     set->stride = std::max<uint32_t>(1, (max_len + kBasesPerWord - 1) / kBasesPerWord);
     set->pair_cells = (sum * sum - sumsq) * 0.5;
+    set->mean_len = n ? sum / (double)n : 0.0;
+    set->id = g_set_ids.fetch_add(1, std::memory_order_relaxed) + 1;
     const uint64_t nbytes = hoff[n] - hoff[0];
     if (nbytes > 0 && !seq) {
         delete set;
@@ -366,8 +486,9 @@ int gbd_tile(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd
         SysJob *d_job = nullptr;
         SysPlan plan;
         if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
-        if ((rc = build_plan(entries, rows, plan, false, st)) != GBD_OK) return rc;
-        rc = run_systolic(d_job, plan, ctx->sm_count, st);
+        if ((rc = build_plan(entries, rows, plan, false, st, 0, B->mean_len, ctx->sm_count)) != GBD_OK)
+            return rc;
+        rc = run_systolic(d_job, plan, ctx->sm_count, st, ctx->aux, ctx->fork, ctx->join);
         cudaFreeAsync(d_job, st);
         free_plan(plan, st);
         if (rc != GBD_OK) return rc;
@@ -404,55 +525,30 @@ int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns, uint16_t
         }
         return GBD_OK;
     }
-    // one plan over every sample's entries, largest first; one launch per length bucket
-    std::vector<SysJob> jobs(ns);
-    std::vector<SysEntry> entries;
-    std::vector<uint8_t> rows;
+    // One plan over every sample's entries, largest first; one launch per length bucket.
+    // The launch group is captured once as a CUDA graph and replayed while the samples
+    // and outputs stay the same.
     for (uint64_t s = 0; s < ns; ++s) {
-        gbd_set *set = const_cast<gbd_set *>(samples[s]);
-        int rc = build_tri_schedule(set, st);
+        int rc = build_tri_schedule(const_cast<gbd_set *>(samples[s]), st);
         if (rc != GBD_OK) return rc;
-        SysJob &job = jobs[s];
-        job = SysJob{};
-        job.Q = job.S = set->view();
-        job.sub_perm = nullptr;
-        job.out = d_tris[s];
-        job.n = set->n;
-        job.mode = OUT_TRI;
-        job.conversion = ctx->params.conversion;
-        const uint64_t n = set->n;
-        for (uint64_t i = 0; i + 1 < n; ++i) {
-            if (set->h_len[i] > kSystolicMaxQuery) continue;
-            entries.push_back({(uint32_t)s, (uint32_t)i, (uint32_t)(i + 1), (uint32_t)(n - 1 - i)});
-            rows.push_back((uint8_t)systolic_rows(set->h_len[i]));
+    }
+    int rc = systolic_prepare();
+    if (rc != GBD_OK) return rc;
+    BatchGraph *bg = static_cast<BatchGraph *>(ctx->batch_cache);
+    bool fresh = false;
+    if (!(bg && bg->matches(samples, ns, d_tris, ctx->params.conversion))) {
+        free_batch_cache(ctx);
+        bg = new BatchGraph();
+        ctx->batch_cache = bg;
+        rc = capture_batch(ctx, bg, samples, ns, d_tris);
+        if (rc != GBD_OK) {
+            free_batch_cache(ctx);
+            return rc;
         }
+        fresh = true;                        // the capture already counted its kernels
     }
-    {
-        std::vector<size_t> order(entries.size());
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(),
-                         [&](size_t x, size_t y) { return entries[x].nsub > entries[y].nsub; });
-        std::vector<SysEntry> e2(entries.size());
-        std::vector<uint8_t> r2(entries.size());
-        for (size_t i = 0; i < order.size(); ++i) { e2[i] = entries[order[i]]; r2[i] = rows[order[i]]; }
-        entries.swap(e2);
-        rows.swap(r2);
-    }
-    int rc = GBD_OK;
-    if (!entries.empty()) {
-        SysJob *d_jobs = nullptr;
-        SysPlan plan;
-        if ((rc = upload(jobs.data(), jobs.size(), &d_jobs, st)) != GBD_OK) return rc;
-        if ((rc = build_plan(entries, rows, plan, false, st)) != GBD_OK) return rc;
-        rc = run_systolic(d_jobs, plan, ctx->sm_count, st);
-        cudaFreeAsync(d_jobs, st);
-        free_plan(plan, st);
-        if (rc != GBD_OK) return rc;
-    }
-    for (uint64_t s = 0; s < ns; ++s) {
-        rc = long_rows_general(ctx, samples[s], d_tris[s], st);
-        if (rc != GBD_OK) return rc;
-    }
+    GBD_CUDA_TRY(cudaGraphLaunch(bg->exec, st));
+    if (!fresh) note_launches(bg->kernels);
     return GBD_OK;
 }
 

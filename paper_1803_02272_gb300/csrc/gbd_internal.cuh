@@ -41,6 +41,7 @@ struct SysPlan {
     struct Bucket {
         int R = 0;
         uint32_t nentries = 0, nunits = 0;
+        uint32_t piece = 1024;                  // subjects per work unit
         size_t entry_off = 0, prefix_off = 0;   // offsets into d_buf (bytes)
     };
     std::vector<Bucket> buckets;
@@ -74,11 +75,16 @@ struct gbd_ctx {
     int device = 0;
     gbd_params params{};
     int sm_count = 0;
+    cudaStream_t aux = nullptr;       // second stream for overlapping bucket launches
+    cudaEvent_t fork = nullptr, join = nullptr;   // fork / join of aux with the caller's stream
+    cudaStream_t capture = nullptr;   // stream that records batch graphs
+    void *batch_cache = nullptr;      // last captured batch graph (api.cu)
 };
 
 struct gbd_set {
     gbd_ctx *ctx = nullptr;
     int device = 0;
+    uint64_t id = 0;            // unique per process (keys cached batch graphs)
     uint64_t n = 0;
     uint32_t stride = 0;        // words per read
     uint32_t max_len = 0;
@@ -86,6 +92,7 @@ struct gbd_set {
     uint16_t *d_len = nullptr;
     std::vector<uint16_t> h_len;
     double pair_cells = 0.0;
+    double mean_len = 0.0;
     gbd::TriSchedule sched;
     gbd::DeviceReads view() const { return {d_words, d_len, n, stride}; }
 };
@@ -126,6 +133,9 @@ int run_general(const GeneralJob &job, const Scoring &sc, int sm_count, cudaStre
 // (scratch_ints ints); allocates nothing.
 int run_general_in(const GeneralJob &job, const Scoring &sc, int *scratch, uint64_t scratch_ints,
                    int sm_count, cudaStream_t stream);
+
+// Frees the context's cached batch graph.
+void free_batch_cache(gbd_ctx *ctx);
 
 // Instruction-rate probe.
 int probe_op_rate(int op, uint32_t iters, double *rate, int sm_count, cudaStream_t stream);

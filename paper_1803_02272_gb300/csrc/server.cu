@@ -36,7 +36,10 @@ namespace {
 
 enum ReqState { REQ_QUEUED = 0, REQ_ACTIVE = 1, REQ_DONE = 2, REQ_FAILED = 3 };
 
-constexpr uint64_t kChunkPairs = 12u << 20;   // ~0.15 s of GPU work per batch
+// Pairs per chunk batch: about 0.15 s of GPU work when few pairs wait (latency), up to
+// 64 Mi pairs when much work is queued (fewer, larger batches keep the GPU saturated).
+constexpr uint64_t kChunkPairs = 12u << 20;
+constexpr uint64_t kMaxChunkPairs = 64u << 20;
 constexpr int kSlots = 2;                     // chunk batches in flight
 
 struct Request {
@@ -80,7 +83,8 @@ struct gbd_server {
     const gbd_set *ref = nullptr;
     cudaStream_t slots[kSlots] = {};
     bool slot_busy[kSlots] = {};
-    cudaStream_t ingest = nullptr;
+    cudaStream_t ingest = nullptr;             // packing and batch uploads
+    cudaEvent_t uploaded[kSlots] = {};         // a slot's uploads are complete
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -166,17 +170,19 @@ std::string admit(gbd_server *srv, Request *r)
 }
 
 // Launches one batch of pieces on stream st; returns an error message or "".
-std::string launch_batch(gbd_server *srv, const std::vector<Piece> &pieces, cudaStream_t st)
+std::string launch_batch(gbd_server *srv, const std::vector<Piece> &pieces, cudaStream_t st,
+                         cudaEvent_t uploaded)
 {
     gbd_ctx *ctx = srv->ctx;
     const gbd_set *ref = srv->ref;
+    cudaStream_t up = srv->ingest;
     const bool systolic = use_systolic_scores(ctx->params);
+    std::vector<GeneralJob> general;
     std::vector<SysJob> jobs;
     std::vector<SysEntry> entries;
     std::vector<uint8_t> rows;
     std::vector<void *> to_free;
     std::string err;
-    uint64_t total_pairs = 0;
     for (const Piece &p : pieces) {
         Request *r = p.req;
         if (r->packed && cudaStreamWaitEvent(st, r->packed, 0) != cudaSuccess) return "cudaStreamWaitEvent failed";
@@ -201,43 +207,44 @@ std::string launch_batch(gbd_server *srv, const std::vector<Piece> &pieces, cuda
                 long_rows.push_back((uint32_t)i);
             }
         }
-        total_pairs += (p.q1 - p.q0) * ref->n;
         if (!long_rows.empty()) {
             uint32_t *d_list = nullptr;
-            if (cudaMallocAsync((void **)&d_list, long_rows.size() * 4, st) != cudaSuccess) return "cudaMallocAsync failed";
+            if (cudaMallocAsync((void **)&d_list, long_rows.size() * 4, up) != cudaSuccess) return "cudaMallocAsync failed";
             to_free.push_back(d_list);
-            if (cudaMemcpyAsync(d_list, long_rows.data(), long_rows.size() * 4, cudaMemcpyHostToDevice, st) !=
+            if (cudaMemcpyAsync(d_list, long_rows.data(), long_rows.size() * 4, cudaMemcpyHostToDevice, up) !=
                 cudaSuccess)
                 return "H2D failed";
             GeneralJob gj{J.Q, J.S, 0, r->nq, 0, ref->n, ref->n, OUT_RECT, r->d_rows};
             gj.rows = d_list;
             gj.nrows = long_rows.size();
-            const Scoring sc{ctx->params.match, ctx->params.mismatch, ctx->params.gap, ctx->params.conversion};
-            if (run_general(gj, sc, ctx->sm_count, st) != GBD_OK) err = gbd_last_error();
+            general.push_back(gj);
         }
     }
-    if (err.empty() && !entries.empty()) {
-        // short pieces of subjects so that even a one-query batch covers every SM
-        const uint64_t warps = (uint64_t)systolic_resident_warps(ctx->sm_count);
-        uint64_t piece = total_pairs / std::max<uint64_t>(1, 4 * warps);
-        piece = std::min<uint64_t>(kSystolicPiece, std::max<uint64_t>(64, piece));
-        SysJob *d_jobs = nullptr;
-        if (cudaMallocAsync((void **)&d_jobs, jobs.size() * sizeof(SysJob), st) == cudaSuccess) {
-            to_free.push_back(d_jobs);
-            if (cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(SysJob), cudaMemcpyHostToDevice, st) ==
-                cudaSuccess) {
-                SysPlan plan;
-                if (build_plan(entries, rows, plan, false, st, (uint32_t)piece) != GBD_OK ||
-                    run_systolic(d_jobs, plan, ctx->sm_count, st) != GBD_OK)
-                    err = gbd_last_error();
-                free_plan(plan, st);
-            } else {
-                err = "H2D failed";
-            }
-        } else {
-            err = "cudaMallocAsync failed";
-        }
+    // Uploads go through the ingest stream, which is idle, so the worker never blocks on
+    // a host copy queued behind the batch still running on this slot's stream.
+    SysJob *d_jobs = nullptr;
+    SysPlan plan;
+    if (!entries.empty()) {
+        // pieces from the cost model: a small batch gets short pieces and still covers
+        // every SM
+        if (cudaMallocAsync((void **)&d_jobs, jobs.size() * sizeof(SysJob), up) != cudaSuccess)
+            return "cudaMallocAsync failed";
+        to_free.push_back(d_jobs);
+        if (cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(SysJob), cudaMemcpyHostToDevice, up) !=
+            cudaSuccess)
+            return "H2D failed";
+        if (build_plan(entries, rows, plan, false, up, 0, ref->mean_len, ctx->sm_count) != GBD_OK)
+            return gbd_last_error();
     }
+    if (cudaEventRecord(uploaded, up) != cudaSuccess || cudaStreamWaitEvent(st, uploaded, 0) != cudaSuccess)
+        err = "upload event failed";
+    const Scoring sc{ctx->params.match, ctx->params.mismatch, ctx->params.gap, ctx->params.conversion};
+    for (const GeneralJob &gj : general)
+        if (err.empty() && run_general(gj, sc, ctx->sm_count, st) != GBD_OK) err = gbd_last_error();
+    if (err.empty() && !entries.empty() && run_systolic(d_jobs, plan, ctx->sm_count, st) != GBD_OK)
+        err = gbd_last_error();
+    plan.stream_ordered = true;
+    free_plan(plan, st);
     for (void *p : to_free) cudaFreeAsync(p, st);
     return err;
 }
@@ -254,7 +261,10 @@ std::vector<Piece> next_pieces(gbd_server *srv)
     });
     std::vector<Piece> out;
     const uint64_t n_ref = srv->ref->n;
-    uint64_t room = std::max<uint64_t>(kChunkPairs / n_ref, 1);   // queries in this batch
+    uint64_t waiting = 0;
+    for (Request *r : cand) waiting += (r->nq - r->next_query) * n_ref;
+    const uint64_t chunk = std::min(kMaxChunkPairs, std::max(kChunkPairs, waiting / 8));
+    uint64_t room = std::max<uint64_t>(chunk / n_ref, 1);         // queries in this batch
     for (Request *r : cand) {
         if (room == 0) break;
         const uint64_t take = std::min<uint64_t>(room, r->nq - r->next_query);
@@ -311,7 +321,7 @@ void worker_main(gbd_server *srv)
             cudaStream_t st = srv->slots[s];
             std::string err;
             try {
-                err = launch_batch(srv, pieces, st);
+                err = launch_batch(srv, pieces, st, srv->uploaded[s]);
             } catch (const std::exception &e) {
                 err = std::string("server batch: ") + e.what();
             }
@@ -360,6 +370,7 @@ int gbd_server_create(gbd_ctx *ctx, const gbd_set *ref, gbd_server **out)
     srv->budget = ctx->params.hbm_budget ? ctx->params.hbm_budget : (uint64_t)(0.9 * (double)free_b);
     for (int i = 0; i < kSlots; ++i) GBD_CUDA_TRY(cudaStreamCreateWithFlags(&srv->slots[i], cudaStreamNonBlocking));
     GBD_CUDA_TRY(cudaStreamCreateWithFlags(&srv->ingest, cudaStreamNonBlocking));
+    for (int i = 0; i < kSlots; ++i) GBD_CUDA_TRY(cudaEventCreateWithFlags(&srv->uploaded[i], cudaEventDisableTiming));
     srv->worker = std::thread(worker_main, srv.get());
     *out = srv.release();
     return GBD_OK;
@@ -479,6 +490,8 @@ void gbd_server_destroy(gbd_server *srv)
         cudaStreamSynchronize(srv->ingest);
         cudaStreamDestroy(srv->ingest);
     }
+    for (int i = 0; i < kSlots; ++i)
+        if (srv->uploaded[i]) cudaEventDestroy(srv->uploaded[i]);
     delete srv;
 }
 

@@ -30,7 +30,9 @@
 // Values are kept in [~1000, ~10700] by rebasing every 8192 steps, so int16 never
 // overflows and 0 acts as minus infinity.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 
 #include "gbd_internal.cuh"
@@ -41,15 +43,18 @@ namespace {
 
 constexpr int LANES = 32;
 constexpr int CH = 16;                       // steps per chunk == lane skew
-constexpr int RING_CHUNKS = 36;              // >= 34 chunks live at once
+// >= 34 chunks are live at once; 48 chunks of 18 words make the ring 864 words, a
+// multiple of the 32 banks, so the lanes' 18-word stride stays conflict-free across the
+// ring's wrap.
+constexpr int RING_CHUNKS = 48;
 constexpr int RING = RING_CHUNKS * CH;       // 576 columns
 constexpr int SLOTS = RING + 3 * CH;         // ring index in [-16, RING + 32)
 // +2 pad words per 16 columns; arrays start on 32-word (128-byte) boundaries so every
 // lane's bank position depends on its column alone
 constexpr int PWORDS = (SLOTS + 2 * (SLOTS / 16) + 31) & ~31;
-constexpr int NARR = 5;                      // profiles for A, C, G, T, and padding rows
-constexpr int TABLE_WORDS = RING_CHUNKS * 8; // per chunk: 8 words of stream metadata
-constexpr int TABLE_OFF = (NARR * PWORDS + 3) & ~3;   // 16-byte aligned table
+constexpr int NARR = 4;                      // per-warp profiles for A, C, G, T
+constexpr int TABLE_WORDS = RING_CHUNKS * 4; // per chunk: 4 words of stream metadata
+constexpr int TABLE_OFF = NARR * PWORDS;
 constexpr int WARP_WORDS = TABLE_OFF + TABLE_WORDS;
 constexpr int WARPS_PER_BLOCK = 2;
 constexpr uint32_t NEG2 = 0xC000C000u;       // (-16384, -16384)
@@ -59,7 +64,12 @@ constexpr int REBASE_CHUNKS = 512;           // 8192 steps
 constexpr uint32_t REBASE2 = 0x20002000u;    // 8192 in both halves
 static_assert(PWORDS % 32 == 0, "profile arrays are 128-byte aligned");
 static_assert((REBASE_CHUNKS & (REBASE_CHUNKS - 1)) == 0, "rebase period is a power of two");
-static_assert(TABLE_OFF % 4 == 0 && WARP_WORDS % 4 == 0, "table and warp regions are 16-byte aligned");
+static_assert(TABLE_OFF % 4 == 0 && WARP_WORDS % 32 == 0, "table and warp regions stay bank-aligned");
+// One never-matching profile per block serves the query rows past a read's end.
+constexpr int NEG_OFF = WARPS_PER_BLOCK * WARP_WORDS;
+constexpr int BLOCK_WORDS = NEG_OFF + PWORDS;
+constexpr int BLOCKS_PER_SM = 6;
+static_assert((RING_CHUNKS * 18) % 32 == 0, "ring length is a multiple of the banks");
 
 // padded word index of ring slot rho (rho in [-16, RING + 32))
 __host__ __device__ constexpr int pslot(int rho) { return (rho + 16) + 2 * ((rho + 16) >> 4); }
@@ -149,7 +159,7 @@ struct ChunkInfo {
     uint32_t word;      // 16 bases, 2 bits each
     uint32_t nvalid;    // valid columns in this chunk (0 = padding chunk)
     uint32_t first, last;
-    uint32_t orig, len;
+    uint32_t orig, len, pos;
 };
 
 __device__ __forceinline__ void cursor_chunk(const Cursor &cu, const SysJob &J, ChunkInfo &ci)
@@ -158,6 +168,7 @@ __device__ __forceinline__ void cursor_chunk(const Cursor &cu, const SysJob &J, 
     ci.first = valid && cu.ck == 0;
     ci.last = valid && cu.ck + 1 == cu.nck;
     ci.orig = cu.orig;
+    ci.pos = cu.pos;
     ci.len = cu.len;
     if (valid) {
         const uint32_t base = cu.ck * 16u;
@@ -191,13 +202,11 @@ __device__ __forceinline__ void fill_chunk(uint32_t *ws, int lane, int m, const 
         if (rho >= RING - 16) arr[pslot(rho - RING)] = v;
     }
     if (lane == 0) {
-        uint32_t *e = ws + TABLE_OFF + 8 * m;
+        uint32_t *e = ws + TABLE_OFF + 4 * m;
         e[0] = (lo.first ? 0x0000ffffu : 0u) | (hi.first ? 0xffff0000u : 0u);
         e[1] = (lo.last ? 0x0000ffffu : 0u) | (hi.last ? 0xffff0000u : 0u);
         e[2] = lo.len | (hi.len << 16);
-        e[3] = 0;
-        e[4] = lo.orig;
-        e[5] = hi.orig;
+        e[3] = (lo.pos & 0xffffu) | (hi.pos << 16);       // position in each half's list
     }
 }
 
@@ -208,7 +217,7 @@ __device__ __forceinline__ uint2 lds64(const uint32_t *ws_words, uint32_t byte_o
 
 template <int R>
 __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint32_t *ws, int lane,
-                                      uint32_t *err)
+                                      int neg_rel, uint32_t *err)
 {
     constexpr int D = CH - R;                 // delay steps between lanes
     const int la = J.Q.len[u.q];
@@ -239,7 +248,7 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
             const int pos = lane * R + r;
             uint32_t code = 4;
             if (pos < la) code = (__ldg(qwords + (pos >> 4)) >> (2 * (pos & 15))) & 3u;
-            addr[r] = (code * PWORDS + P0) * 4u;
+            addr[r] = ((code < 4 ? (int)code * PWORDS : neg_rel) + P0) * 4u;
         }
     }
 
@@ -261,7 +270,7 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
     uint32_t up0_prev = f_prev2;               // row 0's diagonal input
     uint32_t curRel = 0, prevRel = 0, acc = 0, emit = 0;
     uint32_t Mlast_prev = 0;                   // "ends a subject" masks of chunk c-1
-    uint32_t lens_prev = 0, orig_lo_prev = 0, orig_hi_prev = 0;
+    uint32_t lens_prev = 0, pos_prev = 0;
     uint2 sp[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -296,12 +305,12 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
         // ---- this lane's chunk c: stream metadata
         const int c = g - lane;
         uint32_t Mfirst = 0, Mend;                 // Mend: chunk c-1 ended a subject
-        uint32_t lens_c = 0, olo_c = 0, ohi_c = 0, Mlast_c = 0;
+        uint32_t lens_c = 0, pos_c = 0, Mlast_c = 0;
         if (c >= 0) {
-            const uint32_t *e = ws + TABLE_OFF + 8 * m_c;
+            const uint32_t *e = ws + TABLE_OFF + 4 * m_c;
             const uint4 ev = *reinterpret_cast<const uint4 *>(e);
             Mfirst = ev.x; Mlast_c = ev.y; lens_c = ev.z;
-            olo_c = e[4]; ohi_c = e[5];
+            pos_c = ev.w;
         }
         Mend = (c >= 1) ? Mlast_prev : 0xffffffffu;   // c <= 0: discard what came before
         const uint32_t fbase = f_prev + ONE2;         // floor at step 0 of this chunk
@@ -384,7 +393,8 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
                 for (int h = 0; h < 2; ++h) {
                     if ((Mend >> (16 * h)) & 1u) {
                         const int S = (int)(int16_t)(total >> (16 * h));
-                        const uint32_t so = h ? orig_hi_prev : orig_lo_prev;
+                        const uint32_t li = u.sub_begin + h + 2 * ((pos_prev >> (16 * h)) & 0xffffu);
+                        const uint32_t so = J.sub_perm ? __ldg(J.sub_perm + li) : li;
                         const int lb = (int)((lens_prev >> (16 * h)) & 0xffffu);
                         uint64_t idx;
                         if (J.mode == OUT_TRI) {
@@ -400,8 +410,7 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
             }
             Mlast_prev = (c >= 0) ? Mlast_c : 0u;
             lens_prev = lens_c;
-            orig_lo_prev = olo_c;
-            orig_hi_prev = ohi_c;
+            pos_prev = pos_c;
         }
         // ---- advance the profile addresses by one chunk
         {
@@ -416,7 +425,7 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
 }
 
 template <int R>
-__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 7)
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, BLOCKS_PER_SM)
 sw_systolic_kernel(const SysJob *__restrict__ jobs, const SysEntry *__restrict__ entries,
                    const uint32_t *__restrict__ prefix, uint32_t nentries, uint32_t nunits,
                    uint32_t piece_len, uint32_t *counter, uint32_t *err)
@@ -425,8 +434,9 @@ sw_systolic_kernel(const SysJob *__restrict__ jobs, const SysEntry *__restrict__
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     uint32_t *ws = smem + warp * WARP_WORDS;
-    for (int i = lane; i < WARP_WORDS; i += 32) ws[i] = NEG2;
-    __syncwarp();
+    for (int i = threadIdx.x; i < BLOCK_WORDS; i += blockDim.x) smem[i] = NEG2;
+    __syncthreads();
+    const int neg_rel = NEG_OFF - warp * WARP_WORDS;   // block's padding profile, from ws
     for (;;) {
         uint32_t ui = 0;
         if (lane == 0) ui = atomicAdd(counter, 1u);
@@ -445,9 +455,24 @@ sw_systolic_kernel(const SysJob *__restrict__ jobs, const SysEntry *__restrict__
         u.q = en.q;
         u.sub_begin = en.sub_begin + piece * piece_len;
         u.nsub = min(piece_len, en.nsub - piece * piece_len);
-        run_unit<R>(jobs[u.job], u, ws, lane, err);
+        run_unit<R>(jobs[u.job], u, ws, lane, neg_rel, err);
         __syncwarp();
     }
+}
+
+// Blocks per SM of each instantiation (set up before any launch or capture).
+int g_per_sm[17];
+
+template <int R>
+int prepare_bucket()
+{
+    const size_t smem = systolic_smem_bytes();
+    GBD_CUDA_TRY(cudaFuncSetAttribute(sw_systolic_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    GBD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_per_sm[R], sw_systolic_kernel<R>,
+                                                                WARPS_PER_BLOCK * 32, smem));
+    if (g_per_sm[R] < 1) return fail(GBD_ECUDA, "systolic kernel does not fit on an SM");
+    return GBD_OK;
 }
 
 template <int R>
@@ -456,17 +481,7 @@ int launch_bucket(const SysJob *d_jobs, const SysEntry *entries, const uint32_t 
                   uint32_t *err, int sm_count, cudaStream_t stream)
 {
     const size_t smem = systolic_smem_bytes();
-    static bool attr_set = false;
-    if (!attr_set) {
-        GBD_CUDA_TRY(cudaFuncSetAttribute(sw_systolic_kernel<R>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
-    int per_sm = 0;
-    GBD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sw_systolic_kernel<R>,
-                                                                WARPS_PER_BLOCK * 32, smem));
-    if (per_sm < 1) return fail(GBD_ECUDA, "systolic kernel does not fit on an SM");
-    uint64_t blocks = (uint64_t)sm_count * per_sm;
+    uint64_t blocks = (uint64_t)sm_count * g_per_sm[R];
     const uint64_t need = (nunits + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
     if (blocks > need) blocks = need;
     sw_systolic_kernel<R><<<(unsigned)blocks, WARPS_PER_BLOCK * 32, smem, stream>>>(
@@ -479,13 +494,44 @@ int launch_bucket(const SysJob *d_jobs, const SysEntry *entries, const uint32_t 
 
 }  // namespace
 
-size_t systolic_smem_bytes() { return (size_t)WARPS_PER_BLOCK * WARP_WORDS * sizeof(uint32_t); }
+size_t systolic_smem_bytes() { return (size_t)BLOCK_WORDS * sizeof(uint32_t); }
+
+int systolic_prepare()
+{
+    static std::mutex mu;
+    static bool done = false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done) return GBD_OK;
+    int rc = GBD_OK;
+#define GBD_CASE(RR) if (rc == GBD_OK) rc = prepare_bucket<RR>();
+    GBD_CASE(1) GBD_CASE(2) GBD_CASE(3) GBD_CASE(4) GBD_CASE(5) GBD_CASE(6) GBD_CASE(7)
+    GBD_CASE(8) GBD_CASE(9) GBD_CASE(10) GBD_CASE(11) GBD_CASE(12) GBD_CASE(13)
+    GBD_CASE(14) GBD_CASE(15) GBD_CASE(16)
+#undef GBD_CASE
+    if (rc == GBD_OK) done = true;
+    return rc;
+}
+
+// Subjects per work unit for one bucket, from a cost model of the launch: every unit
+// pays the systolic pipeline's fill and drain (32 chunks of 16 steps) once, and the
+// launch ends with a tail of about half a unit on the slowest warp.  With P pairs in the
+// bucket, W resident warps and subjects of mean length L (so a unit of p subjects runs
+// p*L/2 steps on two half streams), the time is proportional to
+//     P*L/(2W) + (P/p)*512/W + p*L/4,
+// minimised at p* = sqrt(2048*P / (W*L)).
+uint32_t tuned_piece(uint64_t pairs, double mean_len, int warps)
+{
+    const double L = mean_len > 16.0 ? mean_len : 16.0;
+    double p = std::sqrt(2048.0 * (double)pairs / ((double)std::max(warps, 1) * L));
+    p = std::min(4096.0, std::max(64.0, p));
+    return ((uint32_t)p + 31u) & ~31u;
+}
 
 int build_plan(const std::vector<SysEntry> &entries, const std::vector<uint8_t> &rows,
-               SysPlan &plan, bool persistent, cudaStream_t stream, uint32_t piece_len)
+               SysPlan &plan, bool persistent, cudaStream_t stream, uint32_t piece_len,
+               double mean_subject_len, int sm_count)
 {
     plan = SysPlan{};
-    if (piece_len == 0) return fail(GBD_EINVAL, "internal: zero piece length");
     plan.piece = piece_len;
     std::vector<std::vector<SysEntry>> by_r(17);
     for (size_t i = 0; i < entries.size(); ++i) {
@@ -497,17 +543,21 @@ int build_plan(const std::vector<SysEntry> &entries, const std::vector<uint8_t> 
     // layout: for each bucket, entries (16 B each) then prefix (nentries + 1 words)
     size_t bytes = 0;
     std::vector<std::vector<uint32_t>> prefixes(17);
+    const int warps = systolic_resident_warps(sm_count);
     for (int R = 16; R >= 1; --R) {          // launch order: widest rows first
         if (by_r[R].empty()) continue;
         SysPlan::Bucket b;
         b.R = R;
         b.nentries = (uint32_t)by_r[R].size();
+        uint64_t pairs = 0;
+        for (const SysEntry &e : by_r[R]) pairs += e.nsub;
+        b.piece = piece_len ? piece_len : tuned_piece(pairs, mean_subject_len, warps);
         std::vector<uint32_t> &pf = prefixes[R];
         pf.resize(b.nentries + 1);
         uint64_t acc = 0;
         for (uint32_t e = 0; e < b.nentries; ++e) {
             pf[e] = (uint32_t)acc;
-            acc += (by_r[R][e].nsub + piece_len - 1) / piece_len;
+            acc += (by_r[R][e].nsub + b.piece - 1) / b.piece;
         }
         if (acc >= 0xffffffffull) return fail(GBD_EINVAL, "too many work units for one launch");
         pf[b.nentries] = (uint32_t)acc;
@@ -545,13 +595,24 @@ void free_plan(SysPlan &plan, cudaStream_t stream)
     plan = SysPlan{};
 }
 
-int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaStream_t stream)
+int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaStream_t stream,
+                 cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join)
 {
     if (plan.buckets.empty()) return GBD_OK;
+    int prc = systolic_prepare();
+    if (prc != GBD_OK) return prc;
     const size_t nb = plan.buckets.size();
     uint32_t *scratch = nullptr;                  // per bucket: work counter, error flags
     GBD_CUDA_TRY(cudaMallocAsync((void **)&scratch, 2 * nb * sizeof(uint32_t), stream));
     GBD_CUDA_TRY(cudaMemsetAsync(scratch, 0, 2 * nb * sizeof(uint32_t), stream));
+    // Buckets alternate between `stream` and `aux`, so the tail of one bucket's launch
+    // overlaps the start of the next (a persistent grid starts where the other's blocks
+    // have exited).  The two streams fork and join on events.
+    const bool two = aux != nullptr && fork != nullptr && join != nullptr && nb > 1;
+    if (two) {
+        GBD_CUDA_TRY(cudaEventRecord(fork, stream));
+        GBD_CUDA_TRY(cudaStreamWaitEvent(aux, fork, 0));
+    }
     int rc = GBD_OK;
     for (size_t i = 0; i < nb && rc == GBD_OK; ++i) {
         const SysPlan::Bucket &b = plan.buckets[i];
@@ -559,14 +620,19 @@ int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaSt
         const SysEntry *en = reinterpret_cast<const SysEntry *>(base + b.entry_off);
         const uint32_t *pf = reinterpret_cast<const uint32_t *>(base + b.prefix_off);
         uint32_t *ctr = scratch + 2 * i, *err = scratch + 2 * i + 1;
+        cudaStream_t st = (two && (i & 1)) ? aux : stream;
         switch (b.R) {
-#define GBD_CASE(RR) case RR: rc = launch_bucket<RR>(d_jobs, en, pf, b.nentries, b.nunits, plan.piece, ctr, err, sm_count, stream); break;
+#define GBD_CASE(RR) case RR: rc = launch_bucket<RR>(d_jobs, en, pf, b.nentries, b.nunits, b.piece, ctr, err, sm_count, st); break;
             GBD_CASE(1) GBD_CASE(2) GBD_CASE(3) GBD_CASE(4) GBD_CASE(5) GBD_CASE(6) GBD_CASE(7)
             GBD_CASE(8) GBD_CASE(9) GBD_CASE(10) GBD_CASE(11) GBD_CASE(12) GBD_CASE(13)
             GBD_CASE(14) GBD_CASE(15) GBD_CASE(16)
 #undef GBD_CASE
             default: rc = fail(GBD_EINVAL, "internal: bad rows per lane");
         }
+    }
+    if (two) {
+        cudaEventRecord(join, aux);
+        cudaStreamWaitEvent(stream, join, 0);
     }
     cudaError_t fe = cudaFreeAsync(scratch, stream);
     if (rc != GBD_OK) return rc;
@@ -579,7 +645,7 @@ int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaSt
 namespace gbd {
 int systolic_resident_warps(int sm_count)
 {
-    // 7 blocks of 2 warps per SM (shared memory bound, see launch_bucket)
-    return sm_count * 7 * WARPS_PER_BLOCK;
+    // shared memory bound: BLOCKS_PER_SM blocks of WARPS_PER_BLOCK warps per SM
+    return sm_count * BLOCKS_PER_SM * WARPS_PER_BLOCK;
 }
 }  // namespace gbd

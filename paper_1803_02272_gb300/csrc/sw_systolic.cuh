@@ -33,14 +33,22 @@ inline int systolic_rows(int la) { return la <= 32 ? 1 : (la + 31) / 32; }
 // Groups entries by R (rows[i] = R of entries[i]) and uploads them.  Entries keep their
 // order inside a bucket (callers put the largest first).  persistent: cudaMalloc (kept
 // with a read set) instead of stream-ordered memory.
+// piece_len == 0: each bucket's piece comes from the cost model (tuned_piece) given the
+// subjects' mean length.
 int build_plan(const std::vector<SysEntry> &entries, const std::vector<uint8_t> &rows,
-               SysPlan &plan, bool persistent, cudaStream_t stream,
-               uint32_t piece_len = kSystolicPiece);
+               SysPlan &plan, bool persistent, cudaStream_t stream, uint32_t piece_len,
+               double mean_subject_len, int sm_count);
+uint32_t tuned_piece(uint64_t pairs, double mean_len, int warps);
 // Number of warps the systolic kernel keeps resident on the whole GPU.
 int systolic_resident_warps(int sm_count);
 void free_plan(SysPlan &plan, cudaStream_t stream);
 
-int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaStream_t stream);
+// aux: optional second stream; consecutive buckets alternate between the two, forking
+// and joining on the events fork / join (owned by the caller; needed when aux is set).
+int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaStream_t stream,
+                 cudaStream_t aux = nullptr, cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 size_t systolic_smem_bytes();
+// Sets kernel attributes and occupancy of every instantiation (once; before any capture).
+int systolic_prepare();
 
 }  // namespace gbd
