@@ -78,6 +78,12 @@ class Stream:
         span = hi - lo + 1
         return (lo + np.floor(self.uniform(shape) * span)).astype(np.int64)
 
+    def normal(self, shape) -> np.ndarray:
+        """Standard normal doubles by the Box-Muller transform of two uniform draws."""
+        u1 = self.uniform(shape)
+        u2 = self.uniform(shape)
+        return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+
     def log_uniform_int(self, lo: int, hi: int, shape) -> np.ndarray:
         """Integers whose logarithm is uniform on [ln lo, ln hi], rounded."""
         u = self.uniform(shape)
