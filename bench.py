@@ -48,12 +48,15 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--mode", choices=["allpairs", "batch", "serve"], default="allpairs")
+    ap.add_argument("--mode", choices=["allpairs", "batch", "serve", "mds"], default="allpairs")
     ap.add_argument("--serve-requests", type=int, default=40,
                     help="requests in the serving phase of the all-pairs run (0 = skip)")
     ap.add_argument("--serve-load", type=float, default=0.8,
                     help="offered load of that phase, as a fraction of measured pairs/s")
     ap.add_argument("--samples", type=int, default=64, help="batch mode: samples")
+    ap.add_argument("--mds-k", type=int, default=64, help="mds mode: sketch columns k")
+    ap.add_argument("--mds-r", type=int, default=50, help="mds mode: coordinates r (paper: 50)")
+    ap.add_argument("--mds-q", type=int, default=2, help="mds mode: subspace-iteration rounds")
     return ap.parse_args(argv)
 
 
@@ -163,15 +166,15 @@ def cpu_oracle_sample(rs, seconds: float, seed: int = 7):
         j = i + 1 + (st_rng.random(k) * (n - 1 - i)).astype(np.int64)
         return i, j
 
-    i, j = sample(4 * cores, seed)
-    t0 = time.perf_counter()
-    oracle.pairs(rs, i, j, nthreads=cores)
-    dt = time.perf_counter() - t0
-    k = int(max(4 * cores, min(2_000_000, len(i) * seconds / max(dt, 1e-6))))
-    i, j = sample(k, seed + 1)
-    t0 = time.perf_counter()
-    oracle.pairs(rs, i, j, nthreads=cores)
-    dt = time.perf_counter() - t0
+    k = 4 * cores
+    for attempt in range(6):           # grow the sample until it takes about `seconds`
+        i, j = sample(k, seed + attempt)
+        t0 = time.perf_counter()
+        oracle.pairs(rs, i, j, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * seconds or k >= 4_000_000:
+            break
+        k = int(min(4_000_000, max(2 * k, k * seconds / max(dt, 1e-6))))
     cells = float(np.sum(L[i] * L[j]))
     return {"value": cells / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{k} uniformly sampled pairs of the same {n}-read workload, "
@@ -373,10 +376,8 @@ def run_gbd(args):
     if args.serve_requests > 0 and rank == 0:
         # served-batch latency: Poisson arrivals against this set, resident
         ref = ctx.load(rs)
-        mean_pairs = 492.0 * n             # mean of log-U[1,4096] batch sizes x n_ref
-        rate = args.serve_load * pairs_per_s / mean_pairs
-        line["serving"] = serve_phase(gbd, ctx, ref, rs, dev, args.serve_requests, rate)
-        line["serving"]["offered_load"] = args.serve_load
+        line["serving"] = serve_phase(gbd, ctx, ref, rs, dev, args.serve_requests,
+                                      load=args.serve_load, capacity_pps=pairs_per_s)
         del ref
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -413,15 +414,20 @@ def percentile(xs, p):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), p)) if len(xs) else None
 
 
-def serve_phase(gbd, ctx, ref_handle, ref_rs, dev, n_requests, rate_per_s, seed=1005,
-                check=True, burst=False):
+def serve_phase(gbd, ctx, ref_handle, ref_rs, dev, n_requests, load=1.0, capacity_pps=1.0,
+                seed=1005, check=True, burst=False):
     """Poisson arrivals of query batches against a resident reference set; returns
-    latency percentiles (submit -> rows complete) and served pairs/s."""
+    latency percentiles (submit -> rows complete) and served pairs/s.  The arrival rate
+    makes the offered pairs/s of this very request sample `load` x `capacity_pps`."""
     import torch
     from paper_1803_02272_gb300 import synth
-    reqs = synth.workload_served_queries(n_requests, rate_per_s, seed=seed)
-    srv = gbd.Server(ctx, ref_handle)
+    reqs = synth.workload_served_queries(n_requests, 1.0, seed=seed)   # arrivals at rate 1/s
     n_ref = ref_rs.n
+    mean_pairs = float(np.mean([r.reads.n for r in reqs])) * n_ref
+    rate_per_s = load * capacity_pps / mean_pairs
+    for r in reqs:                     # Poisson gaps scale as 1/rate
+        r.arrival_s = r.arrival_s / rate_per_s
+    srv = gbd.Server(ctx, ref_handle)
     pending, lat, outs = {}, [], []
     t0 = time.perf_counter()
     i = 0
@@ -464,6 +470,7 @@ def serve_phase(gbd, ctx, ref_handle, ref_rs, dev, n_requests, rate_per_s, seed=
     del outs
     nq = [r.reads.n for r in reqs]
     return {"requests": len(reqs), "mean_queries": float(np.mean(nq)),
+            "offered_load": None if burst else load, "rate_per_s": None if burst else rate_per_s,
             "p50_ms": percentile(lat, 50) * 1e3, "p99_ms": percentile(lat, 99) * 1e3,
             "pairs_per_s": total_pairs / wall, "wall_s": wall,
             "spot_check_mismatches": mism}
@@ -534,18 +541,157 @@ def run_serve_mode(args):
         ctx.tile(qh, 0, qh.n, ref, 0, ref.n, out=out.view(-1))
     torch.cuda.synchronize()
     plain_pps = total_pairs / (time.perf_counter() - t0)
-    burst = serve_phase(gbd, ctx, ref, ref_rs, dev, args.serve_requests, 1.0, seed=1006,
+    burst = serve_phase(gbd, ctx, ref, ref_rs, dev, args.serve_requests, seed=1006,
                         check=True, burst=True)
     loads = {}
-    mean_pairs = total_pairs / len(reqs)
     for load in (0.5, 0.8, 0.95):
-        rate = load * burst["pairs_per_s"] / mean_pairs
-        loads[str(load)] = serve_phase(gbd, ctx, ref, ref_rs, dev, args.serve_requests, rate,
-                                       seed=2000 + int(load * 100))
+        loads[str(load)] = serve_phase(gbd, ctx, ref, ref_rs, dev, args.serve_requests, load=load,
+                                       capacity_pps=burst["pairs_per_s"], seed=2000 + int(load * 100))
     line = {"mode": "serve", "reference_reads": ref_rs.n, "requests": len(reqs),
             "plain_sequential_pairs_per_s": plain_pps, "server_burst": burst,
             "server_under_load": loads,
             "server_vs_plain": burst["pairs_per_s"] / plain_pps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def mds_cpu_sample(n_full: int, k: int, r: int, q: int, n_sample: int = 2000):
+    """Time the oracle's randomized MDS on an n_sample-read synthetic triangle; the
+    oracle forms G with two dense n x n products (O(n^3)), so the full-size figure is
+    extrapolated as n^3."""
+    from oracle import mds as omds
+    from paper_1803_02272_gb300 import synth
+    m = n_sample * (n_sample - 1) // 2
+    tri = synth.Stream(91, 0).integers(0, 450, (m,)).astype(np.uint16)
+    omega = synth.Stream(92, 0).normal((n_sample, k))
+    t0 = time.perf_counter()
+    omds.mds_randomized(omds.tri_to_square(tri, n_sample), r, omega, q)
+    dt = time.perf_counter() - t0
+    scale = (n_full / n_sample) ** 3
+    return {"value": dt * scale, "unit": "s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"oracle randomized MDS of a {n_sample}-read triangle (k={k}, r={r}, q={q}) "
+                      f"in {dt:.2f} s, extrapolated by (n/{n_sample})^3 to n={n_full}"}
+
+
+def run_mds_mode(args):
+    """Classical MDS (sections 3 and 6.2) of the paper-scale distance triangle: gbd_mds timed per
+    call, the tensor-core G X product timed alone for its HBM roofline."""
+    import torch
+    from paper_1803_02272_gb300 import gbd, synth
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n, k, r, q = args.n, args.mds_k, args.mds_r, args.mds_q
+    rs = synth.workload_paper_scale(n=n, len_lo=args.len_lo, len_hi=args.len_hi)
+    ctx = gbd.Context(0)
+    s_h = ctx.load(rs)
+    t0 = time.perf_counter()
+    tri = ctx.all_pairs(s_h)
+    torch.cuda.synchronize()
+    allpairs_s = time.perf_counter() - t0
+    omega = torch.from_numpy(synth.Stream(1003, 9).normal((n, k)).astype(np.float32)).to(dev)
+    lam = torch.empty(r, dtype=torch.float32, device=dev)
+    X = torch.empty((n, r), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    for _ in range(args.warmup):
+        gbd.gbd_mds(ctx.handle, tri, n, omega, k, r, q, lam, X, stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    launches0 = gbd.gbd_kernel_launches()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        gbd.gbd_mds(ctx.handle, tri, n, omega, k, r, q, lam, X, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    launches = gbd.gbd_kernel_launches() - launches0
+
+    # the dominant kernel alone: W X on the tensor cores (inside gbd_gram_apply)
+    ld = (n + 127) // 128 * 128
+    W = torch.empty(ld * ld, dtype=torch.int16, device=dev)
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    shift = gbd.gbd_sqdist_square(ctx.handle, tri, n, W, ld, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    square_s = e0.elapsed_time(e1) / 1e3
+    Y = torch.empty((n, k), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        gbd.gbd_gram_apply(ctx.handle, W, n, ld, shift, omega, k, Y, stream)
+    prod = []
+    for _ in range(5):
+        flush.zero_()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        gbd.gbd_gram_apply(ctx.handle, W, n, ld, shift, omega, k, Y, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prod.append(e0.elapsed_time(e1) / 1e3)
+    clocks = sampler.stop()
+    prod_s = float(np.mean(prod))
+    prod_bytes = ld * ld * 2 + k * ld * 2 + n * k * 4 * 2
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    hbm = float(peaks["hbm_gbs"])
+
+    # properties of this very output (any size): sorted eigenvalues, centred and
+    # mutually orthogonal coordinate columns with squared norms equal to the eigenvalues
+    lam_h = lam.cpu().numpy().astype(np.float64)
+    Xh = X.cpu().numpy().astype(np.float64)
+    xtx = Xh.T @ Xh
+    pos = lam_h > 1e-6 * lam_h[0]
+    props = {"sorted": bool(np.all(np.diff(lam_h) <= 0)),
+             "max_rel_norm_err": float(np.max(np.abs(np.diag(xtx)[pos] - lam_h[pos]) / lam_h[pos])),
+             "max_rel_offdiag": float(np.abs(xtx - np.diag(np.diag(xtx))).max() / lam_h[0]),
+             "max_rel_colsum": float(np.abs(Xh.sum(0)).max() / np.sqrt(lam_h[0] * n))}
+    del W, Y
+
+    # end to end through the C ABI with host buffers: triangle in from pinned host memory,
+    # eigenvalues and coordinates back
+    tri_h = torch.empty(tri.numel(), dtype=torch.int16, pin_memory=True)
+    tri_h.copy_(tri)
+    tri_d = torch.empty_like(tri)
+    X_h = torch.empty((n, r), dtype=torch.float32, pin_memory=True)
+    lam_hh = torch.empty(r, dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tri_d.copy_(tri_h, non_blocking=True)
+    gbd.gbd_mds(ctx.handle, tri_d, n, omega, k, r, q, lam, X, stream)
+    X_h.copy_(X, non_blocking=True)
+    lam_hh.copy_(lam, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+
+    t_mds = float(np.mean(times))
+    line = {
+        "metric": f"classical MDS time, n={n} reads, r={r} (randomized SVD, k={k}, q={q})",
+        "value": t_mds, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_mds * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp16 products, f32/f64 accumulation", "data": "synthetic",
+        "config": {"workload": f"classical MDS (sections 3, 6.2) of the all-pairs SW distance triangle "
+                               f"of {n} paper-scale synthetic reads", "n_reads": n, "k": k, "r": r,
+                   "q": q, "square_bytes": ld * ld * 2,
+                   "l2": "fp16 square (20 GB at n=1e5) far larger than L2; 512 MiB flush between steps"},
+        "roofline": {"bound": "hbm", "achieved": prod_bytes / prod_s / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": prod_bytes / prod_s / 1e9 / hbm, "traffic": None,
+                     "kernel": "w_times_x_kernel (tcgen05 + TMA), timed with the rest of one G X call",
+                     "peak_source": "of measured: MEASURED_PEAKS hbm_gbs (copy)"},
+        "g_times_x_ms": prod_s * 1e3, "sqdist_square_ms": square_s * 1e3,
+        "sqdist_square_gbs": (n * (n - 1) + ld * ld * 2) / square_s / 1e9,
+        "allpairs_input_s": allpairs_s, "clocks": clocks, "gpu_launches": int(launches // max(args.steps, 1)),
+        "properties": props,
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(tri.numel() * 2),
+                "d2h_bytes_per_step": int(n * r * 4 + r * 4)},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = mds_cpu_sample(n, k, r, q)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -558,6 +704,8 @@ def main(argv=None):
         return run_batch_mode(args)
     if args.mode == "serve":
         return run_serve_mode(args)
+    if args.mode == "mds":
+        return run_mds_mode(args)
     return run_gbd(args)
 
 

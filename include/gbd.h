@@ -143,6 +143,45 @@ int gbd_tile_noalloc(gbd_ctx *ctx, const uint8_t *d_seqA, const uint64_t *d_offA
                      const uint8_t *d_seqB, const uint64_t *d_offB, uint64_t nB,
                      uint32_t max_len, uint16_t *d_out, uint64_t ld, void *stream);
 
+/* ---------------------------------------------------------------- MDS (paper sections 3 and 6.2)
+ * Classical multidimensional scaling of the distance triangle: Torgerson's double
+ * centering turns the squared distances into the Gram matrix of scalar products
+ *   G = -1/2 J (D o D) J,  J = I - 11^T/n            (section 6.2, step 1),
+ * whose leading eigenpairs (lambda_a, u_a) give the coordinates X = U Lambda^(1/2)
+ * (section 6.2, steps 2-3); the eigenpairs come from a randomized SVD (sections 3.2-3.3, after
+ * Halko, Martinsson and Tropp 2011).  Readings: randomized subspace iteration with q
+ * rounds (each round multiplies by G twice, G being symmetric, with an
+ * orthonormalisation after every product), then B = Q^T G Q and its eigendecomposition;
+ * eigenpairs ordered by eigenvalue, largest first; a negative eigenvalue (distances that
+ * are not Euclidean) gives zero coordinates.
+ *
+ * gbd_sqdist_square: W[i*ld + j] = fp16(d_ij^2 * 2^-s) for i, j < n (W[i*ld+i] = 0), and
+ *   0 in the padding rows and columns up to ld; d_tri is the device triangle in the layout
+ *   of gbd_all_pairs (n(n-1)/2 entries, may be NULL when n < 2); d_w is a device buffer of
+ *   ld*ld uint16 (fp16 bit patterns), ld a multiple of 128 and >= n.  s >= 0 is the
+ *   smallest shift that keeps the largest squared distance below the fp16 maximum and is
+ *   written to *shift (host pointer).  The call synchronises `stream` once to read the
+ *   maximum distance.  EINVAL on a NULL pointer or a bad ld.
+ * gbd_gram_apply: Y = G X for an n x k float32 row-major X (device), from the W of
+ *   gbd_sqdist_square (same n, ld, shift): X is centred and rounded to fp16, W X runs on
+ *   the tensor cores with float32 accumulation, the product is centred and scaled by
+ *   -2^(s-1).  k is a multiple of 16, 16 <= k <= 256.  Y (device, n x k float32) must not
+ *   overlap X.
+ * gbd_mds: the whole MDS for an n-read triangle (the paper uses r = 50, section 4.1): r leading eigenvalues into
+ *   d_lambda (device, r float32, largest first) and the n x r coordinates into d_coords
+ *   (device, float32 row-major).  d_omega is the caller's n x k Gaussian test matrix
+ *   (device, float32 row-major; the library draws no random numbers), r <= k, k as above,
+ *   k < n, q >= 0 rounds.  The library allocates its workspace on `stream` (the fp16 square,
+ *   ld^2 * 2 bytes with ld = n rounded up to 128 -- 20 GB at n = 1e5 -- plus O(n k)) and
+ *   frees it before returning; ENOMEM if it does not fit.  The call synchronises `stream`
+ *   at its end (it reads back convergence and error flags).  EINVAL on bad sizes. */
+int gbd_sqdist_square(gbd_ctx *ctx, const uint16_t *d_tri, uint64_t n, uint16_t *d_w, uint64_t ld,
+                      int32_t *shift, void *stream);
+int gbd_gram_apply(gbd_ctx *ctx, const uint16_t *d_w, uint64_t n, uint64_t ld, int32_t shift,
+                   const float *d_x, uint32_t k, float *d_y, void *stream);
+int gbd_mds(gbd_ctx *ctx, const uint16_t *d_tri, uint64_t n, const float *d_omega, uint32_t k,
+            uint32_t r, uint32_t q, float *d_lambda, float *d_coords, void *stream);
+
 /* Thread-local text of the last error raised on the calling thread ("" if none). */
 const char *gbd_last_error(void);
 

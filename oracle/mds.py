@@ -6,11 +6,11 @@ this module; the library never does, and this module imports nothing from the li
 Plain numpy in float64, dense n x n matrices, so it is meant for n up to a few thousand.
 
 What it follows (arxiv 1803.02272):
-  * section 3.1 (classical MDS, after Torgerson): the scalar products <x_i, x_j> are
+  * section 6.2 (classical MDS, after Torgerson): the scalar products <x_i, x_j> are
     recovered from the distances alone by double centering of the squared distances,
     giving the Gram matrix G; its eigenpairs (lambda_a, u_a), lambda_1 >= lambda_2 >= ...,
     give the coordinates X = U Lambda^(1/2), of which the first r columns are kept;
-  * section 3.2-3.3 (the paper's contribution): the first r eigenpairs come from a
+  * sections 3.2-3.3 (the paper's contribution): the first r eigenpairs come from a
     randomized SVD (Halko, Martinsson and Tropp 2011) instead of a full eigensolver,
     using that for a symmetric matrix the singular values are |lambda|.
 
@@ -43,7 +43,7 @@ def tri_to_square(tri, n: int) -> np.ndarray:
 
 
 def gram(D: np.ndarray) -> np.ndarray:
-    """G = -1/2 J (D o D) J with J = I - 11^T/n (section 3.1: double centering of the
+    """G = -1/2 J (D o D) J with J = I - 11^T/n (section 6.2, step 1: double centering of the
     squared distances; entry (i, j) is the scalar product <x_i, x_j>)."""
     D = np.asarray(D, dtype=np.float64)
     n = D.shape[0]
@@ -60,7 +60,7 @@ def _top(lam: np.ndarray, U: np.ndarray, r: int):
 
 
 def mds_exact(D: np.ndarray, r: int):
-    """Classical MDS with a full symmetric eigensolver (section 3.1).
+    """Classical MDS with a full symmetric eigensolver (section 6.2, steps 1-3).
     Returns (lambda[r], U[n, r], X[n, r])."""
     G = gram(D)
     lam, U = np.linalg.eigh(G)

@@ -1,0 +1,685 @@
+// Classical MDS of the distance triangle (paper sections 3 and 6.2): double centering of
+// the squared distances into the Gram matrix G = -1/2 J (D o D) J (section 6.2) and its
+// leading eigenpairs by randomized SVD (sections 3.2-3.3, after Halko, Martinsson and
+// Tropp 2011: randomized subspace iteration, then B = Q^T G Q and its eigenvectors).
+//
+// Device pipeline:
+//   tri_max_kernel        largest distance (sets the fp16 scale 2^-s)
+//   sqdist_square_kernel  triangle -> ld x ld fp16 W = d^2 2^-s (both halves, zero padding)
+//   G X                   column means of X, centred fp16 X^T, W X^T on the tensor cores
+//                         (mds_gemm.cu), slice sum, column means of the product, and
+//                         Y = -2^(s-1) (P - 1 mean^T); J W J X = J W (J X) needs no
+//                         centred copy of W
+//   orthonormalise        Gram S = Y^T Y (float64), S = V diag(s) V^T by cyclic Jacobi,
+//                         Q = Y V diag(s^-1/2) (directions with s below a floor dropped),
+//                         twice
+//   eigenpairs of B       B = Q^T (G Q) by the same Gram kernel, Jacobi, eigenvalues
+//                         sorted down, coordinates Q V_r diag(max(lambda, 0)^1/2)
+// All reductions run in a fixed order, so results do not depend on scheduling.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gbd_internal.cuh"
+#include "mds_internal.cuh"
+
+namespace gbd {
+namespace {
+
+// ------------------------------------------------------------------ triangle maximum
+__global__ void tri_max_kernel(const uint16_t *__restrict__ tri, uint64_t m, uint32_t *out)
+{
+    uint32_t best = 0;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+    // scalar head up to a 16-byte boundary, uint4 body, scalar tail
+    const uint64_t head = std::min<uint64_t>(m, ((16 - (reinterpret_cast<uintptr_t>(tri) & 15)) & 15) / 2);
+    for (uint64_t i = tid; i < head; i += nthr) best = max(best, (uint32_t)tri[i]);
+    const uint64_t nvec = (m - head) / 8;
+    const uint4 *v = reinterpret_cast<const uint4 *>(tri + head);
+    for (uint64_t i = tid; i < nvec; i += nthr) {
+        const uint4 w = __ldg(v + i);
+        const uint32_t a = __vmaxu2(__vmaxu2(w.x, w.y), __vmaxu2(w.z, w.w));
+        best = max(best, max(a & 0xffffu, a >> 16));
+    }
+    for (uint64_t i = head + nvec * 8 + tid; i < m; i += nthr) best = max(best, (uint32_t)tri[i]);
+    best = __reduce_max_sync(0xffffffffu, best);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+}
+
+// ------------------------------------------------------------------ triangle -> fp16 square
+constexpr int ST = 64;   // square tile
+
+__device__ __forceinline__ uint64_t tri_index(uint64_t i, uint64_t j, uint64_t n)
+{
+    return i * n - i * (i + 1) / 2 + (j - i - 1);
+}
+
+__device__ __forceinline__ uint16_t sq_half(uint32_t d, float scale)
+{
+    const float f = (float)d;
+    return __half_as_ushort(__float2half_rn(f * f * scale));
+}
+
+// Tile (I, J), I <= J, of the square: W[I-block][J-block] from the triangle, and its
+// transpose W[J-block][I-block] through shared memory.
+__global__ void __launch_bounds__(256)
+sqdist_square_kernel(const uint16_t *__restrict__ tri, uint64_t n, uint64_t ld, float scale,
+                     uint16_t *__restrict__ W, uint64_t ntiles)
+{
+    __shared__ uint16_t t[ST][ST + 2];
+    const uint64_t T = ld / ST;
+    const uint64_t lin = blockIdx.x;
+    if (lin >= ntiles) return;
+    // row I of the tile triangle holds T - I tiles
+    const double b = 2.0 * (double)T + 1.0;
+    int64_t I = (int64_t)((b - sqrt(fmax(b * b - 8.0 * (double)lin, 0.0))) * 0.5);
+    auto row_start = [&](int64_t r) { return (uint64_t)r * T - (uint64_t)r * (uint64_t)(r - 1) / 2; };
+    if (I < 0) I = 0;
+    while (I > 0 && row_start(I) > lin) --I;
+    while ((uint64_t)(I + 1) < T && row_start(I + 1) <= lin) ++I;
+    const uint64_t J = (uint64_t)I + (lin - row_start(I));
+    const uint64_t i0 = (uint64_t)I * ST, j0 = J * ST;
+
+    // each thread: 4 consecutive columns of one row, 4 passes of 16 rows
+    const int c4 = (threadIdx.x & 15) * 4;
+    for (int r = threadIdx.x >> 4; r < ST; r += 16) {
+        const uint64_t i = i0 + r;
+        uint16_t v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint64_t j = j0 + c4 + e;
+            uint16_t h = 0;
+            if (i < n && j < n && i != j) {
+                const uint32_t d = (i < j) ? tri[tri_index(i, j, n)] : tri[tri_index(j, i, n)];
+                h = sq_half(d, scale);
+            }
+            v[e] = h;
+            t[r][c4 + e] = h;
+        }
+        uint2 pk;
+        pk.x = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
+        pk.y = (uint32_t)v[2] | ((uint32_t)v[3] << 16);
+        *reinterpret_cast<uint2 *>(W + i * ld + j0 + c4) = pk;
+    }
+    if ((uint64_t)I == J) return;
+    __syncthreads();
+    for (int r = threadIdx.x >> 4; r < ST; r += 16) {
+        uint2 pk;
+        pk.x = (uint32_t)t[c4][r] | ((uint32_t)t[c4 + 1][r] << 16);
+        pk.y = (uint32_t)t[c4 + 2][r] | ((uint32_t)t[c4 + 3][r] << 16);
+        *reinterpret_cast<uint2 *>(W + (j0 + r) * ld + i0 + c4) = pk;
+    }
+}
+
+// ------------------------------------------------------------------ column means
+constexpr int kSumBlocks = 256;
+
+// partial[b][c] = sum of X[i][c] over the rows of block b (fixed row ranges).
+__global__ void colsum_partial_kernel(const float *__restrict__ X, uint64_t n, uint32_t k, double *partial)
+{
+    const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const uint64_t r0 = blockIdx.x * per, r1 = std::min<uint64_t>(n, r0 + per);
+    for (uint32_t c = threadIdx.x; c < k; c += blockDim.x) {
+        double s = 0.0;
+        for (uint64_t i = r0; i < r1; ++i) s += (double)X[i * k + c];
+        partial[(uint64_t)blockIdx.x * k + c] = s;
+    }
+}
+
+__global__ void colmean_final_kernel(const double *__restrict__ partial, uint32_t nparts, uint32_t k, uint64_t n,
+                                     double *mean)
+{
+    for (uint32_t c = threadIdx.x; c < k; c += blockDim.x) {
+        double s = 0.0;
+        for (uint32_t b = 0; b < nparts; ++b) s += partial[(uint64_t)b * k + c];
+        mean[c] = s / (double)n;
+    }
+}
+
+// Xt[c][i] = fp16(X[i][c] - mean[c]) for i < n; 0 for n <= i < ld.  32 x 32 tiles.
+__global__ void center_transpose_kernel(const float *__restrict__ X, const double *__restrict__ mean, uint64_t n,
+                                        uint64_t ld, uint32_t k, uint16_t *__restrict__ Xt)
+{
+    __shared__ float t[32][33];
+    const uint64_t i0 = (uint64_t)blockIdx.x * 32;
+    const uint32_t c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const uint64_t i = i0 + r;
+        const uint32_t c = c0 + threadIdx.x;
+        float v = 0.f;
+        if (i < n && c < k) v = (float)((double)X[i * k + c] - mean[c]);
+        t[r][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const uint32_t c = c0 + r;
+        const uint64_t i = i0 + threadIdx.x;
+        if (c < k && i < ld) Xt[(uint64_t)c * ld + i] = __half_as_ushort(__float2half_rn(t[threadIdx.x][r]));
+    }
+}
+
+// P[i][c] = sum over slices s (in order) of part[s][i][c], i < n.
+__global__ void slice_sum_kernel(const float *__restrict__ part, uint32_t slices, uint64_t n, uint64_t ld,
+                                 uint32_t k, float *__restrict__ P)
+{
+    const uint64_t total = n * k;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (uint32_t q = 0; q < slices; ++q) s += part[(uint64_t)q * ld * k + e];
+        P[e] = s;
+    }
+}
+
+// Y = alpha (P - 1 mean^T)
+__global__ void center_scale_kernel(const float *__restrict__ P, const double *__restrict__ mean, uint64_t n,
+                                    uint32_t k, double alpha, float *__restrict__ Y)
+{
+    const uint64_t total = n * k;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (uint64_t)gridDim.x * blockDim.x)
+        Y[e] = (float)(alpha * ((double)P[e] - mean[e % k]));
+}
+
+// ------------------------------------------------------------------ A^T B in float64
+constexpr int kGramRows = 32;
+
+// partial[b] = sum over block b's rows of A[i]^T B[i] (k x k, float64 products of the
+// float32 inputs, exact), in a fixed order.
+__global__ void __launch_bounds__(256)
+xty_partial_kernel(const float *__restrict__ A, const float *__restrict__ B, uint64_t n, uint32_t k,
+                   double *partial)
+{
+    extern __shared__ float sm[];
+    float *As = sm;                       // [kGramRows][k]
+    float *Bs = sm + kGramRows * k;       // [kGramRows][k]
+    const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const uint64_t r0 = blockIdx.x * per, r1 = std::min<uint64_t>(n, r0 + per);
+    const uint32_t kk = k * k;
+    double *out = partial + (uint64_t)blockIdx.x * kk;
+    for (uint32_t o0 = 0; o0 < kk; o0 += blockDim.x * 16) {
+        double acc[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) acc[t] = 0.0;
+        for (uint64_t rb = r0; rb < r1; rb += kGramRows) {
+            const uint32_t rows = (uint32_t)std::min<uint64_t>(kGramRows, r1 - rb);
+            __syncthreads();
+            for (uint32_t e = threadIdx.x; e < rows * k; e += blockDim.x) {
+                As[e] = A[rb * k + e];
+                Bs[e] = B[rb * k + e];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const uint32_t o = o0 + threadIdx.x + t * blockDim.x;
+                if (o < kk) {
+                    const uint32_t a = o / k, b = o % k;
+                    double s = acc[t];
+                    for (uint32_t r = 0; r < rows; ++r) s += (double)As[r * k + a] * (double)Bs[r * k + b];
+                    acc[t] = s;
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const uint32_t o = o0 + threadIdx.x + t * blockDim.x;
+            if (o < kk) out[o] = acc[t];
+        }
+    }
+}
+
+__global__ void xty_final_kernel(const double *__restrict__ partial, uint32_t nparts, uint32_t kk, double *C)
+{
+    for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < kk; o += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (uint32_t b = 0; b < nparts; ++b) s += partial[(uint64_t)b * kk + o];
+        C[o] = s;
+    }
+}
+
+// ------------------------------------------------------------------ symmetric eigensolver
+// Cyclic Jacobi with the round-robin ordering (k/2 disjoint rotations per round, k-1
+// rounds per sweep), float64, one block.  mode 0 (orthonormalisation of Y, S = Y^T Y):
+// T = V diag(w), w = s^-1/2 where s > floor * max s, else 0.  mode 1 (eigenpairs of B):
+// the r largest eigenvalues in order into lambda, T = V_r diag(max(lambda, 0)^1/2).
+// flags bit 0: Jacobi did not converge; bit 1: non-finite input.
+constexpr int kMaxJacobiK = 112;
+constexpr int kMaxSweeps = 40;
+
+__global__ void __launch_bounds__(256)
+jacobi_kernel(const double *__restrict__ S_in, uint32_t k, int mode, uint32_t r, double floor_rel,
+              float *__restrict__ T, float *__restrict__ lambda, uint32_t *flags)
+{
+    extern __shared__ double sd[];
+    double *A = sd;                   // k x k
+    double *V = sd + k * k;           // k x k
+    __shared__ double cs[kMaxJacobiK / 2], sn[kMaxJacobiK / 2];
+    __shared__ int pp[kMaxJacobiK / 2], qq[kMaxJacobiK / 2];
+    __shared__ double red[256];
+    __shared__ int done;
+    __shared__ int order[kMaxJacobiK];
+    const uint32_t kk = k * k;
+    for (uint32_t e = threadIdx.x; e < kk; e += blockDim.x) {
+        const uint32_t i = e / k, j = e % k;
+        const double a = 0.5 * (S_in[i * k + j] + S_in[j * k + i]);
+        A[e] = a;
+        V[e] = (i == j) ? 1.0 : 0.0;
+        if (!isfinite(a)) atomicOr(flags, 2u);
+    }
+    __syncthreads();
+    const uint32_t half = k / 2;
+    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+        // convergence test: off-diagonal mass against the total
+        double off = 0.0, tot = 0.0;
+        for (uint32_t e = threadIdx.x; e < kk; e += blockDim.x) {
+            const double a = A[e];
+            tot += a * a;
+            if (e / k != e % k) off += a * a;
+        }
+        red[threadIdx.x] = off;
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        const double off_sum = red[0];
+        __syncthreads();
+        red[threadIdx.x] = tot;
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) done = (off_sum <= 1e-30 * red[0]) || off_sum == 0.0;
+        __syncthreads();
+        if (done) break;
+        if (sweep == kMaxSweeps - 1) {
+            if (threadIdx.x == 0) atomicOr(flags, 1u);
+            break;
+        }
+        for (uint32_t round = 0; round + 1 < k; ++round) {
+            if (threadIdx.x < half) {
+                // circle method: position 0 fixed, positions 1..k-1 rotate
+                auto at = [&](uint32_t pos) -> uint32_t { return pos == 0 ? 0u : 1u + (pos - 1 + round) % (k - 1); };
+                uint32_t p = at(threadIdx.x), q = at(k - 1 - threadIdx.x);
+                if (p > q) { const uint32_t t = p; p = q; q = t; }
+                const double apq = A[p * k + q];
+                double c = 1.0, s = 0.0;
+                if (apq != 0.0) {
+                    const double theta = (A[q * k + q] - A[p * k + p]) / (2.0 * apq);
+                    const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                    c = 1.0 / sqrt(t * t + 1.0);
+                    s = t * c;
+                }
+                cs[threadIdx.x] = c;
+                sn[threadIdx.x] = s;
+                pp[threadIdx.x] = (int)p;
+                qq[threadIdx.x] = (int)q;
+            }
+            __syncthreads();
+            // columns: A <- A P, V <- V P
+            for (uint32_t e = threadIdx.x; e < half * k; e += blockDim.x) {
+                const uint32_t pr = e / k, row = e % k;
+                const int p = pp[pr], q = qq[pr];
+                const double c = cs[pr], s = sn[pr];
+                const double ap = A[row * k + p], aq = A[row * k + q];
+                A[row * k + p] = c * ap - s * aq;
+                A[row * k + q] = s * ap + c * aq;
+                const double vp = V[row * k + p], vq = V[row * k + q];
+                V[row * k + p] = c * vp - s * vq;
+                V[row * k + q] = s * vp + c * vq;
+            }
+            __syncthreads();
+            // rows: A <- P^T A
+            for (uint32_t e = threadIdx.x; e < half * k; e += blockDim.x) {
+                const uint32_t pr = e / k, col = e % k;
+                const int p = pp[pr], q = qq[pr];
+                const double c = cs[pr], s = sn[pr];
+                const double ap = A[p * k + col], aq = A[q * k + col];
+                A[p * k + col] = c * ap - s * aq;
+                A[q * k + col] = s * ap + c * aq;
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    // eigenvalues on the diagonal; rank them largest first (ties by index)
+    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
+        const double li = A[i * k + i];
+        int rank = 0;
+        for (uint32_t j = 0; j < k; ++j) {
+            const double lj = A[j * k + j];
+            if (lj > li || (lj == li && j < i)) ++rank;
+        }
+        order[rank] = (int)i;
+    }
+    __syncthreads();
+    if (mode == 0) {
+        const double smax = A[order[0] * k + order[0]];
+        for (uint32_t e = threadIdx.x; e < kk; e += blockDim.x) {
+            const uint32_t row = e / k, col = e % k;
+            const double s = A[col * k + col];
+            const double w = (s > floor_rel * smax && s > 0.0) ? 1.0 / sqrt(s) : 0.0;
+            T[e] = (float)(V[row * k + col] * w);
+        }
+    } else {
+        for (uint32_t e = threadIdx.x; e < k * r; e += blockDim.x) {
+            const uint32_t row = e / r, a = e % r;
+            const int col = order[a];
+            const double lam = A[col * k + col];
+            T[e] = (float)(V[row * k + col] * sqrt(fmax(lam, 0.0)));
+        }
+        for (uint32_t a = threadIdx.x; a < r; a += blockDim.x) lambda[a] = (float)A[order[a] * k + order[a]];
+    }
+}
+
+// ------------------------------------------------------------------ Out = A T
+// A: n x k (row-major), T: k x m, Out: n x m.  64 rows per block, float32.
+__global__ void __launch_bounds__(256)
+apply_kernel(const float *__restrict__ A, const float *__restrict__ T, uint64_t n, uint32_t k, uint32_t m,
+             float *__restrict__ Out)
+{
+    extern __shared__ float sa[];
+    float *As = sa;                     // [64][k + 1]
+    float *Ts = sa + 64 * (k + 1);      // [k][m]
+    const uint64_t r0 = (uint64_t)blockIdx.x * 64;
+    for (uint32_t e = threadIdx.x; e < 64 * k; e += blockDim.x) {
+        const uint32_t r = e / k, c = e % k;
+        As[r * (k + 1) + c] = (r0 + r < n) ? A[(r0 + r) * k + c] : 0.f;
+    }
+    for (uint32_t e = threadIdx.x; e < k * m; e += blockDim.x) Ts[e] = T[e];
+    __syncthreads();
+    const uint32_t r = threadIdx.x & 63;
+    if (r0 + r >= n) return;
+    for (uint32_t c = threadIdx.x >> 6; c < m; c += 4) {
+        float s = 0.f;
+        for (uint32_t j = 0; j < k; ++j) s = fmaf(As[r * (k + 1) + j], Ts[j * m + c], s);
+        Out[(r0 + r) * m + c] = s;
+    }
+}
+
+// ------------------------------------------------------------------ host helpers
+int grid_for(uint64_t work, int threads, int sm_count)
+{
+    const uint64_t want = (work + threads - 1) / threads;
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(sm_count, 1) * 8));
+}
+
+#define GBD_LAUNCH_CHECK(name)                                   \
+    do {                                                         \
+        note_launches(1);                                        \
+        cudaError_t _le = cudaGetLastError();                    \
+        if (_le != cudaSuccess) return cuda_fail(_le, name);     \
+    } while (0)
+
+// Workspace of the G X product and of the orthonormalisation.
+struct MdsWork {
+    uint64_t n = 0, ld = 0;
+    uint32_t k = 0, slices = 0;
+    uint16_t *xt = nullptr;       // k x ld fp16
+    float *part = nullptr;        // slices x ld x k
+    float *P = nullptr;           // n x k
+    double *sums = nullptr;       // kSumBlocks x k
+    double *mean = nullptr;       // k
+    double *gram_part = nullptr;  // gram_blocks x k x k
+    double *gram = nullptr;       // k x k
+    float *T = nullptr;           // k x k
+    uint32_t *flags = nullptr;    // [0] product error word, [1] eigensolver flags
+    uint32_t gram_blocks = 0;
+    cudaStream_t st = nullptr;
+    std::vector<void *> owned;
+
+    int alloc(void **p, size_t bytes)
+    {
+        cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(GBD_ENOMEM, std::string("device workspace of ") + std::to_string(bytes) + " bytes: " +
+                                        cudaGetErrorString(e));
+        }
+        owned.push_back(*p);
+        return GBD_OK;
+    }
+    int init(uint64_t n_, uint64_t ld_, uint32_t k_, int sm_count, cudaStream_t s)
+    {
+        n = n_; ld = ld_; k = k_; st = s;
+        slices = w_times_x_slices(ld, sm_count);
+        gram_blocks = (uint32_t)std::min<uint64_t>(256, std::max<uint64_t>(1, (n + 255) / 256));
+        int rc = alloc((void **)&xt, (size_t)k * ld * 2);
+        if (rc == GBD_OK) rc = alloc((void **)&part, (size_t)slices * ld * k * 4);
+        if (rc == GBD_OK) rc = alloc((void **)&P, (size_t)n * k * 4);
+        if (rc == GBD_OK) rc = alloc((void **)&sums, (size_t)kSumBlocks * k * 8);
+        if (rc == GBD_OK) rc = alloc((void **)&mean, (size_t)k * 8);
+        if (rc == GBD_OK) rc = alloc((void **)&gram_part, (size_t)gram_blocks * k * k * 8);
+        if (rc == GBD_OK) rc = alloc((void **)&gram, (size_t)k * k * 8);
+        if (rc == GBD_OK) rc = alloc((void **)&T, (size_t)k * k * 4);
+        if (rc == GBD_OK) rc = alloc((void **)&flags, 16);
+        if (rc == GBD_OK) {
+            cudaError_t e = cudaMemsetAsync(flags, 0, 16, st);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        }
+        return rc;
+    }
+    void release()
+    {
+        for (void *p : owned) cudaFreeAsync(p, st);
+        owned.clear();
+    }
+};
+
+int column_means(const float *X, uint64_t n, uint32_t k, MdsWork &w)
+{
+    colsum_partial_kernel<<<kSumBlocks, 128, 0, w.st>>>(X, n, k, w.sums);
+    GBD_LAUNCH_CHECK("colsum_partial_kernel");
+    colmean_final_kernel<<<1, 128, 0, w.st>>>(w.sums, kSumBlocks, k, n, w.mean);
+    GBD_LAUNCH_CHECK("colmean_final_kernel");
+    return GBD_OK;
+}
+
+// Y = G X (G = -1/2 J (D o D) J with D o D = 2^s W).
+int gram_apply_in(const uint16_t *W, int32_t shift, const float *X, float *Y, MdsWork &w, int sm_count)
+{
+    int rc = column_means(X, w.n, w.k, w);
+    if (rc != GBD_OK) return rc;
+    dim3 tg((unsigned)(w.ld / 32), (w.k + 31) / 32);
+    center_transpose_kernel<<<tg, dim3(32, 8), 0, w.st>>>(X, w.mean, w.n, w.ld, w.k, w.xt);
+    GBD_LAUNCH_CHECK("center_transpose_kernel");
+    rc = w_times_x(W, w.ld, w.xt, w.k, w.part, w.slices, w.flags, sm_count, w.st);
+    if (rc != GBD_OK) return rc;
+    slice_sum_kernel<<<grid_for(w.n * w.k, 256, sm_count), 256, 0, w.st>>>(w.part, w.slices, w.n, w.ld, w.k, w.P);
+    GBD_LAUNCH_CHECK("slice_sum_kernel");
+    rc = column_means(w.P, w.n, w.k, w);
+    if (rc != GBD_OK) return rc;
+    const double alpha = -std::ldexp(1.0, shift - 1);
+    center_scale_kernel<<<grid_for(w.n * w.k, 256, sm_count), 256, 0, w.st>>>(w.P, w.mean, w.n, w.k, alpha, Y);
+    GBD_LAUNCH_CHECK("center_scale_kernel");
+    return GBD_OK;
+}
+
+int xty(const float *A, const float *B, MdsWork &w)
+{
+    const size_t smem = 2 * (size_t)kGramRows * w.k * sizeof(float);
+    xty_partial_kernel<<<w.gram_blocks, 256, smem, w.st>>>(A, B, w.n, w.k, w.gram_part);
+    GBD_LAUNCH_CHECK("xty_partial_kernel");
+    xty_final_kernel<<<(w.k * w.k + 255) / 256, 256, 0, w.st>>>(w.gram_part, w.gram_blocks, w.k * w.k, w.gram);
+    GBD_LAUNCH_CHECK("xty_final_kernel");
+    return GBD_OK;
+}
+
+size_t jacobi_smem(uint32_t k) { return 2 * (size_t)k * k * sizeof(double); }
+
+int apply(const float *A, const float *T, uint32_t m, float *Out, MdsWork &w)
+{
+    const size_t smem = (64 * (size_t)(w.k + 1) + (size_t)w.k * m) * sizeof(float);
+    apply_kernel<<<(unsigned)((w.n + 63) / 64), 256, smem, w.st>>>(A, T, w.n, w.k, m, Out);
+    GBD_LAUNCH_CHECK("apply_kernel");
+    return GBD_OK;
+}
+
+// Q = orthonormal basis of the range of Y (two eigen-based passes).  Y is overwritten.
+constexpr double kOrthFloor = 1e-12;
+
+int orthonormalise(float *Y, float *Q, MdsWork &w)
+{
+    float *src = Y, *dst = Q;
+    for (int pass = 0; pass < 2; ++pass) {
+        int rc = xty(src, src, w);
+        if (rc != GBD_OK) return rc;
+        jacobi_kernel<<<1, 256, jacobi_smem(w.k), w.st>>>(w.gram, w.k, 0, 0, kOrthFloor, w.T, nullptr, w.flags + 1);
+        GBD_LAUNCH_CHECK("jacobi_kernel");
+        rc = apply(src, w.T, w.k, dst, w);
+        if (rc != GBD_OK) return rc;
+        std::swap(src, dst);
+    }
+    // two passes: the result is back in Y; copy to Q
+    cudaError_t e = cudaMemcpyAsync(Q, Y, w.n * w.k * sizeof(float), cudaMemcpyDeviceToDevice, w.st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    return GBD_OK;
+}
+
+int configure_kernels()
+{
+    static std::mutex mu;
+    static bool done = false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done) return GBD_OK;
+    GBD_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)jacobi_smem(kMaxJacobiK)));
+    GBD_CUDA_TRY(cudaFuncSetAttribute(xty_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(2 * kGramRows * kMaxJacobiK * sizeof(float))));
+    GBD_CUDA_TRY(cudaFuncSetAttribute(
+        apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)((64 * (kMaxJacobiK + 1) + kMaxJacobiK * kMaxJacobiK) * sizeof(float))));
+    done = true;
+    return GBD_OK;
+}
+
+int sqdist_square_impl(gbd_ctx *ctx, const uint16_t *d_tri, uint64_t n, uint16_t *d_w, uint64_t ld,
+                       int32_t *shift, cudaStream_t st)
+{
+    if (!ctx || !d_w || !shift) return fail(GBD_EINVAL, "NULL argument");
+    if (n >= 2 && !d_tri) return fail(GBD_EINVAL, "NULL triangle");
+    if (ld == 0 || ld % 128 != 0 || ld < n) return fail(GBD_EINVAL, "ld must be a multiple of 128 and >= n");
+    if (n > 0xffffffffull) return fail(GBD_EINVAL, "too many reads");
+    GBD_CUDA_TRY(cudaSetDevice(ctx->device));
+    const uint64_t m = n < 2 ? 0 : n * (n - 1) / 2;
+    uint32_t dmax = 0;
+    if (m > 0) {
+        uint32_t *d_max = nullptr;
+        GBD_CUDA_TRY(cudaMallocAsync((void **)&d_max, sizeof(uint32_t), st));
+        GBD_CUDA_TRY(cudaMemsetAsync(d_max, 0, sizeof(uint32_t), st));
+        tri_max_kernel<<<grid_for(m / 8 + 1, 256, ctx->sm_count), 256, 0, st>>>(d_tri, m, d_max);
+        note_launches(1);
+        cudaError_t le = cudaGetLastError();
+        cudaError_t ce = cudaMemcpyAsync(&dmax, d_max, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+        cudaError_t se = cudaStreamSynchronize(st);
+        cudaFreeAsync(d_max, st);
+        if (le != cudaSuccess) return cuda_fail(le, "tri_max_kernel launch");
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemcpyAsync");
+        if (se != cudaSuccess) return cuda_fail(se, "cudaStreamSynchronize");
+    }
+    // smallest s >= 0 with dmax^2 * 2^-s <= 65504 (the fp16 maximum)
+    int s = 0;
+    const double d2 = (double)dmax * (double)dmax;
+    while (d2 * std::ldexp(1.0, -s) > 65504.0) ++s;
+    *shift = s;
+    const uint64_t T = ld / ST;
+    const uint64_t ntiles = T * (T + 1) / 2;
+    if (ntiles > 0x7fffffffull) return fail(GBD_EINVAL, "square too large");
+    sqdist_square_kernel<<<(unsigned)ntiles, 256, 0, st>>>(d_tri, n, ld, (float)std::ldexp(1.0, -s), d_w, ntiles);
+    GBD_LAUNCH_CHECK("sqdist_square_kernel");
+    return GBD_OK;
+}
+
+int read_flags(MdsWork &w)
+{
+    uint32_t h[2] = {0, 0};
+    GBD_CUDA_TRY(cudaMemcpyAsync(h, w.flags, sizeof(h), cudaMemcpyDeviceToHost, w.st));
+    GBD_CUDA_TRY(cudaStreamSynchronize(w.st));
+    if (h[0] != 0)
+        return fail(GBD_ETIMEDOUT, "tensor-core product: a bounded wait ran out (code " + std::to_string(h[0]) + ")");
+    if (h[1] & 2u) return fail(GBD_EINVAL, "eigensolver: non-finite input");
+    if (h[1] & 1u) return fail(GBD_ECUDA, "eigensolver: Jacobi sweeps did not converge");
+    return GBD_OK;
+}
+
+}  // namespace
+}  // namespace gbd
+
+using namespace gbd;
+
+extern "C" int gbd_sqdist_square(gbd_ctx *ctx, const uint16_t *d_tri, uint64_t n, uint16_t *d_w, uint64_t ld,
+                                 int32_t *shift, void *stream)
+{
+    return sqdist_square_impl(ctx, d_tri, n, d_w, ld, shift, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int gbd_gram_apply(gbd_ctx *ctx, const uint16_t *d_w, uint64_t n, uint64_t ld, int32_t shift,
+                              const float *d_x, uint32_t k, float *d_y, void *stream)
+{
+    if (!ctx || !d_w || !d_x || !d_y) return fail(GBD_EINVAL, "NULL argument");
+    if (ld == 0 || ld % 128 != 0 || ld < n || n == 0) return fail(GBD_EINVAL, "need 0 < n <= ld, ld a multiple of 128");
+    if (k < 16 || k > 256 || k % 16 != 0) return fail(GBD_EINVAL, "k must be a multiple of 16 in [16, 256]");
+    if (shift < 0 || shift > 64) return fail(GBD_EINVAL, "bad shift");
+    const size_t xb = n * k * sizeof(float);
+    const uintptr_t x0 = reinterpret_cast<uintptr_t>(d_x), y0 = reinterpret_cast<uintptr_t>(d_y);
+    if (x0 < y0 + xb && y0 < x0 + xb) return fail(GBD_EINVAL, "X and Y overlap");
+    GBD_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MdsWork w;
+    int rc = w.init(n, ld, k, ctx->sm_count, st);
+    if (rc == GBD_OK) rc = gram_apply_in(d_w, shift, d_x, d_y, w, ctx->sm_count);
+    int frc = (rc == GBD_OK) ? read_flags(w) : rc;
+    w.release();
+    return frc;
+}
+
+extern "C" int gbd_mds(gbd_ctx *ctx, const uint16_t *d_tri, uint64_t n, const float *d_omega, uint32_t k,
+                       uint32_t r, uint32_t q, float *d_lambda, float *d_coords, void *stream)
+{
+    if (!ctx || !d_tri || !d_omega || !d_lambda || !d_coords) return fail(GBD_EINVAL, "NULL argument");
+    if (k < 16 || k > (uint32_t)kMaxJacobiK || k % 16 != 0)
+        return fail(GBD_EINVAL, "k must be a multiple of 16 in [16, 112]");
+    if (r == 0 || r > k) return fail(GBD_EINVAL, "need 0 < r <= k");
+    if (n <= k) return fail(GBD_EINVAL, "need n > k");
+    if (q > 16) return fail(GBD_EINVAL, "at most 16 rounds");
+    GBD_CUDA_TRY(cudaSetDevice(ctx->device));
+    int rc = configure_kernels();
+    if (rc != GBD_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint64_t ld = (n + 127) / 128 * 128;
+    MdsWork w;
+    uint16_t *W = nullptr;
+    float *Y = nullptr, *Q = nullptr;
+    int32_t shift = 0;
+    rc = w.init(n, ld, k, ctx->sm_count, st);
+    if (rc == GBD_OK) rc = w.alloc((void **)&W, (size_t)ld * ld * 2);
+    if (rc == GBD_OK) rc = w.alloc((void **)&Y, (size_t)n * k * 4);
+    if (rc == GBD_OK) rc = w.alloc((void **)&Q, (size_t)n * k * 4);
+    if (rc == GBD_OK) rc = sqdist_square_impl(ctx, d_tri, n, W, ld, &shift, st);
+    // range finder: Q = orth(G Omega), then q rounds of two products (G is symmetric)
+    if (rc == GBD_OK) rc = gram_apply_in(W, shift, d_omega, Y, w, ctx->sm_count);
+    if (rc == GBD_OK) rc = orthonormalise(Y, Q, w);
+    for (uint32_t t = 0; rc == GBD_OK && t < 2 * q; ++t) {
+        rc = gram_apply_in(W, shift, Q, Y, w, ctx->sm_count);
+        if (rc == GBD_OK) rc = orthonormalise(Y, Q, w);
+    }
+    // B = Q^T G Q, eigenpairs, coordinates Q V_r diag(sqrt(max(lambda, 0)))
+    if (rc == GBD_OK) rc = gram_apply_in(W, shift, Q, Y, w, ctx->sm_count);
+    if (rc == GBD_OK) rc = xty(Q, Y, w);
+    if (rc == GBD_OK) {
+        jacobi_kernel<<<1, 256, jacobi_smem(k), st>>>(w.gram, k, 1, r, 0.0, w.T, d_lambda, w.flags + 1);
+        note_launches(1);
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) rc = cuda_fail(le, "jacobi_kernel launch");
+    }
+    if (rc == GBD_OK) rc = apply(Q, w.T, r, d_coords, w);
+    int frc = (rc == GBD_OK) ? read_flags(w) : rc;
+    w.release();
+    return frc;
+}

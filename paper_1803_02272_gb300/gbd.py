@@ -32,7 +32,7 @@ EXPORTS = [
     "gbd_set_size", "gbd_set_max_len", "gbd_set_pair_cells", "gbd_all_pairs", "gbd_tile",
     "gbd_batch", "gbd_server_create", "gbd_server_submit", "gbd_server_poll",
     "gbd_server_wait", "gbd_server_destroy", "gbd_last_error", "gbd_probe_op_rate",
-    "gbd_kernel_launches", "gbd_tile_noalloc",
+    "gbd_kernel_launches", "gbd_tile_noalloc", "gbd_sqdist_square", "gbd_gram_apply", "gbd_mds",
 ]
 
 
@@ -73,6 +73,9 @@ def _declare(lib):
         "gbd_probe_op_rate": ([ci, u32, ctypes.POINTER(ctypes.c_double), vp], ci),
         "gbd_kernel_launches": ([], u64),
         "gbd_tile_noalloc": ([vp, vp, vp, u64, vp, vp, u64, u32, vp, u64, vp], ci),
+        "gbd_sqdist_square": ([vp, vp, u64, vp, u64, ctypes.POINTER(ctypes.c_int32), vp], ci),
+        "gbd_gram_apply": ([vp, vp, u64, u64, ctypes.c_int32, vp, u32, vp, vp], ci),
+        "gbd_mds": ([vp, vp, u64, vp, u32, u32, u32, vp, vp, vp], ci),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -215,6 +218,25 @@ def gbd_tile_noalloc(ctx: int, seqA, offA, nA: int, seqB, offB, nB: int, max_len
     """Allocation-free rectangle (device inputs and output; see include/gbd.h)."""
     _check(_lib.gbd_tile_noalloc(ctx, _ptr(seqA), _ptr(offA), nA, _ptr(seqB), _ptr(offB), nB,
                                  max_len, _ptr(d_out), ld, _stream(stream)))
+
+
+def gbd_sqdist_square(ctx: int, d_tri, n: int, d_w, ld: int, stream=None) -> int:
+    """fp16 square of scaled squared distances from a triangle; returns the shift s."""
+    s = ctypes.c_int32()
+    _check(_lib.gbd_sqdist_square(ctx, _ptr(d_tri), n, _ptr(d_w), ld, ctypes.byref(s), _stream(stream)))
+    return s.value
+
+
+def gbd_gram_apply(ctx: int, d_w, n: int, ld: int, shift: int, d_x, k: int, d_y, stream=None) -> None:
+    """Y = G X with G = -1/2 J (D o D) J (device float32 n x k)."""
+    _check(_lib.gbd_gram_apply(ctx, _ptr(d_w), n, ld, shift, _ptr(d_x), k, _ptr(d_y), _stream(stream)))
+
+
+def gbd_mds(ctx: int, d_tri, n: int, d_omega, k: int, r: int, q: int, d_lambda, d_coords,
+            stream=None) -> None:
+    """Classical MDS by randomized SVD: r eigenvalues and n x r coordinates (device)."""
+    _check(_lib.gbd_mds(ctx, _ptr(d_tri), n, _ptr(d_omega), k, r, q, _ptr(d_lambda), _ptr(d_coords),
+                        _stream(stream)))
 
 
 def gbd_kernel_launches() -> int:

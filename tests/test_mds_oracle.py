@@ -2,7 +2,7 @@
 
 * Euclidean point clouds: classical MDS recovers the centred Gram matrix exactly, so
   G = Xc Xc^T, the non-zero eigenvalues are those of Xc^T Xc and the rest vanish
-  (Torgerson; section 3.1 of the paper).
+  (Torgerson; section 6.2 of the paper).
 * Points on a line with integer coordinates give an integer distance triangle whose MDS
   is the centred coordinate itself, up to sign.
 * The triangle layout, by hand on n = 4.
