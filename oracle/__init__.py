@@ -10,7 +10,9 @@ It wraps two plain C files, compiled with gcc on first use (or by `build()`):
     (paper section 2.2);
   * brute.c     -- the local score by listing every alignment of every pair of
     substrings, with no DP table, used to pin sw_oracle.c on tiny reads.
-Default scores: match +1, mismatch -1, linear gap -1 (the paper states none).
+Default scores: match +1, mismatch -1, linear gap -1 (the paper states none); an
+optional affine mode (gap_open > 0: a run of L gapped bases costs gap_open + L * gap,
+Gotoh's recurrence) pinned by its own brute force.
 """
 from __future__ import annotations
 
@@ -62,20 +64,24 @@ def _load():
             lib.oracle_distance.restype = ci
             lib.oracle_tri_index.argtypes = [ctypes.c_uint64] * 3
             lib.oracle_tri_index.restype = ctypes.c_uint64
-            lib.oracle_all_pairs.argtypes = [u8p, u64p, ctypes.c_uint64, u16p, ci, ci, ci, ci]
+            lib.oracle_sw_score_affine.argtypes = [u8p, i64, u8p, i64, ci, ci, ci, ci]
+            lib.oracle_sw_score_affine.restype = ci
+            lib.oracle_all_pairs.argtypes = [u8p, u64p, ctypes.c_uint64, u16p, ci, ci, ci, ci, ci]
             lib.oracle_pairs.argtypes = [u8p, u64p, u8p, u64p, u64p, u64p, ctypes.c_uint64, u16p,
-                                         ci, ci, ci, ci]
+                                         ci, ci, ci, ci, ci]
             lib.oracle_pair_scores.argtypes = [u8p, u64p, u8p, u64p, u64p, u64p, ctypes.c_uint64,
-                                               ctypes.POINTER(ctypes.c_int32), ci, ci, ci, ci]
+                                               ctypes.POINTER(ctypes.c_int32), ci, ci, ci, ci, ci]
             lib.oracle_rect.argtypes = [u8p, u64p, ctypes.c_uint64, ctypes.c_uint64, u8p, u64p,
                                         ctypes.c_uint64, ctypes.c_uint64, u16p, ctypes.c_uint64,
-                                        ci, ci, ci, ci]
+                                        ci, ci, ci, ci, ci]
             lib.brute_local_score.argtypes = [u8p, ci, u8p, ci, ci, ci, ci]
             lib.brute_local_score.restype = ci
+            lib.brute_local_score_affine.argtypes = [u8p, ci, u8p, ci, ci, ci, ci, ci]
+            lib.brute_local_score_affine.restype = ci
             lib.brute_count_strings.argtypes = [ci]
             lib.brute_count_strings.restype = ci
             lib.brute_string.argtypes = [ci, ci, u8p, ctypes.POINTER(ci)]
-            lib.brute_exhaustive.argtypes = [ci, ci, ci, ci, ctypes.POINTER(ctypes.c_int32)]
+            lib.brute_exhaustive.argtypes = [ci, ci, ci, ci, ci, ctypes.POINTER(ctypes.c_int32)]
             _lib = lib
     return _lib
 
@@ -119,18 +125,19 @@ def _seq_off(rs):
     return seq, np.ascontiguousarray(rs.offsets, dtype=np.uint64)
 
 
-def all_pairs(rs, match=MATCH, mismatch=MISMATCH, gap=GAP, nthreads=None) -> np.ndarray:
+def all_pairs(rs, match=MATCH, mismatch=MISMATCH, gap=GAP, nthreads=None, gap_open=0) -> np.ndarray:
     """Strict upper triangle (row-major, uint16) of all pairwise distances of a ReadSet."""
     n = rs.n
     out = np.zeros(max(n * (n - 1) // 2, 1), dtype=np.uint16)
     seq, off = _seq_off(rs)
     _load().oracle_all_pairs(_ptr(seq, ctypes.c_uint8), _ptr(off, ctypes.c_uint64), n,
-                             _ptr(out, ctypes.c_uint16), match, mismatch, gap, _threads(nthreads))
+                             _ptr(out, ctypes.c_uint16), match, mismatch, gap, gap_open,
+                             _threads(nthreads))
     return out[: n * (n - 1) // 2]
 
 
 def pairs(rsA, pi, pj, rsB=None, match=MATCH, mismatch=MISMATCH, gap=GAP,
-          nthreads=None) -> np.ndarray:
+          nthreads=None, gap_open=0) -> np.ndarray:
     """out[p] = d(A[pi[p]], B[pj[p]]) (B defaults to A)."""
     rsB = rsA if rsB is None else rsB
     pi = np.ascontiguousarray(pi, dtype=np.uint64)
@@ -141,12 +148,13 @@ def pairs(rsA, pi, pj, rsB=None, match=MATCH, mismatch=MISMATCH, gap=GAP,
     _load().oracle_pairs(_ptr(sa, ctypes.c_uint8), _ptr(oa, ctypes.c_uint64),
                          _ptr(sb, ctypes.c_uint8), _ptr(ob, ctypes.c_uint64),
                          _ptr(pi, ctypes.c_uint64), _ptr(pj, ctypes.c_uint64), len(pi),
-                         _ptr(out, ctypes.c_uint16), match, mismatch, gap, _threads(nthreads))
+                         _ptr(out, ctypes.c_uint16), match, mismatch, gap, gap_open,
+                         _threads(nthreads))
     return out[: len(pi)]
 
 
 def pair_scores(rsA, pi, pj, rsB=None, match=MATCH, mismatch=MISMATCH, gap=GAP,
-                nthreads=None) -> np.ndarray:
+                nthreads=None, gap_open=0) -> np.ndarray:
     """out[p] = S(A[pi[p]], B[pj[p]]), the raw local alignment score (int32)."""
     rsB = rsA if rsB is None else rsB
     pi = np.ascontiguousarray(pi, dtype=np.uint64)
@@ -157,12 +165,13 @@ def pair_scores(rsA, pi, pj, rsB=None, match=MATCH, mismatch=MISMATCH, gap=GAP,
     _load().oracle_pair_scores(_ptr(sa, ctypes.c_uint8), _ptr(oa, ctypes.c_uint64),
                                _ptr(sb, ctypes.c_uint8), _ptr(ob, ctypes.c_uint64),
                                _ptr(pi, ctypes.c_uint64), _ptr(pj, ctypes.c_uint64), len(pi),
-                               _ptr(out, ctypes.c_int32), match, mismatch, gap, _threads(nthreads))
+                               _ptr(out, ctypes.c_int32), match, mismatch, gap, gap_open,
+                               _threads(nthreads))
     return out[: len(pi)]
 
 
 def rect(rsA, a0, a1, rsB, b0, b1, match=MATCH, mismatch=MISMATCH, gap=GAP,
-         nthreads=None) -> np.ndarray:
+         nthreads=None, gap_open=0) -> np.ndarray:
     """Row-major (a1-a0) x (b1-b0) block of distances d(A[r], B[c])."""
     ld = b1 - b0
     out = np.zeros(max((a1 - a0) * ld, 1), dtype=np.uint16)
@@ -170,7 +179,8 @@ def rect(rsA, a0, a1, rsB, b0, b1, match=MATCH, mismatch=MISMATCH, gap=GAP,
     sb, ob = _seq_off(rsB)
     _load().oracle_rect(_ptr(sa, ctypes.c_uint8), _ptr(oa, ctypes.c_uint64), a0, a1,
                         _ptr(sb, ctypes.c_uint8), _ptr(ob, ctypes.c_uint64), b0, b1,
-                        _ptr(out, ctypes.c_uint16), ld, match, mismatch, gap, _threads(nthreads))
+                        _ptr(out, ctypes.c_uint16), ld, match, mismatch, gap, gap_open,
+                        _threads(nthreads))
     return out[: (a1 - a0) * ld].reshape(a1 - a0, ld)
 
 
@@ -181,6 +191,20 @@ def brute_score(a, b, match=MATCH, mismatch=MISMATCH, gap=GAP) -> int:
     A, B = _bytes(a), _bytes(b)
     return _load().brute_local_score(_ptr(A, ctypes.c_uint8), len(a), _ptr(B, ctypes.c_uint8),
                                      len(b), match, mismatch, gap)
+
+
+def sw_score_affine(a, b, gap_open, gap=GAP, match=MATCH, mismatch=MISMATCH) -> int:
+    """Local score with affine gaps (Gotoh): a run of L gapped bases costs gap_open + L*gap."""
+    A, B = _bytes(a), _bytes(b)
+    return _load().oracle_sw_score_affine(_ptr(A, ctypes.c_uint8), len(a), _ptr(B, ctypes.c_uint8),
+                                          len(b), match, mismatch, gap_open, gap)
+
+
+def brute_score_affine(a, b, gap_open, gap=GAP, match=MATCH, mismatch=MISMATCH) -> int:
+    """Brute force with affine gap runs (no DP table)."""
+    A, B = _bytes(a), _bytes(b)
+    return _load().brute_local_score_affine(_ptr(A, ctypes.c_uint8), len(a), _ptr(B, ctypes.c_uint8),
+                                            len(b), match, mismatch, gap_open, gap)
 
 
 def brute_strings(maxlen: int) -> list[bytes]:
@@ -196,12 +220,12 @@ def brute_strings(maxlen: int) -> list[bytes]:
     return out
 
 
-def brute_exhaustive(maxlen: int, match=MATCH, mismatch=MISMATCH, gap=GAP) -> np.ndarray:
+def brute_exhaustive(maxlen: int, match=MATCH, mismatch=MISMATCH, gap=GAP, gap_open=0) -> np.ndarray:
     """Matrix of brute-force scores over all string pairs of length <= maxlen."""
     lib = _load()
     ns = lib.brute_count_strings(maxlen)
     out = np.zeros(ns * ns, dtype=np.int32)
-    lib.brute_exhaustive(maxlen, match, mismatch, gap, _ptr(out, ctypes.c_int32))
+    lib.brute_exhaustive(maxlen, match, mismatch, gap, gap_open, _ptr(out, ctypes.c_int32))
     return out.reshape(ns, ns)
 
 

@@ -187,3 +187,56 @@ def test_rect_matches_pairs():
     R = oracle.rect(A, 2, 15, B, 1, 13)
     ii, jj = np.meshgrid(np.arange(2, 15), np.arange(1, 13), indexing="ij")
     np.testing.assert_array_equal(R.ravel(), oracle.pairs(A, ii.ravel(), jj.ravel(), B))
+
+
+# ------------------------------------------------------------------ affine gaps (Gotoh)
+
+@pytest.mark.parametrize("scores", [(1, -1, 1, 2), (2, -3, 1, 3), (1, -2, 2, 1)])
+def test_affine_exhaustive_len4(scores):
+    """Affine mode (a run of L gapped bases costs gap_open + L * gap) against the brute
+    force that charges each gap run explicitly, on every pair of reads of length <= 4."""
+    m, x, g, go = scores
+    strings = oracle.brute_strings(4)
+    brute = oracle.brute_exhaustive(4, m, x, g, go)
+    rs = _strings_readset(strings)
+    n = len(strings)
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    S = oracle.pair_scores(rs, ii.ravel(), jj.ravel(), match=m, mismatch=x, gap=g, gap_open=go)
+    np.testing.assert_array_equal(S, brute.ravel())
+
+
+def test_affine_by_hand_and_limits():
+    # one gap of length 2: AAAAGGTTTT vs AAAATTTT, 8 matches - (open + 2 * extend)
+    assert oracle.sw_score_affine("AAAAGGTTTT", "AAAATTTT", gap_open=1, gap=1) == 8 - 3
+    assert oracle.brute_score_affine("AAAAGGTTTT", "AAAATTTT", gap_open=1, gap=1) == 5
+    # shorter flanks: the gapped alignment (6 - 3) loses to the gap-free AAAA (4)
+    assert oracle.sw_score_affine("AAAAGGTT", "AAAATT", gap_open=1, gap=1) == 4
+    # under a large open penalty the best local alignment avoids the gap (AAAA or TTTT)
+    assert oracle.sw_score_affine("AAAAGGTTTT", "AAAATTTT", gap_open=5, gap=1) == 4
+    # gap_open = 0 is the linear model
+    st = synth.Stream(31, 1)
+    for _ in range(200):
+        la, lb = (int(v) for v in st.integers(0, 12, (2,)))
+        a = "".join("ACGT"[c] for c in synth.random_codes(st, (la,)))
+        b = "".join("ACGT"[c] for c in synth.random_codes(st, (lb,)))
+        assert oracle.sw_score_affine(a, b, gap_open=0, gap=1) == oracle.sw_score(a, b)
+        # a positive open penalty never raises the score, and never lowers it below the
+        # best gap-free segment
+        assert oracle.sw_score_affine(a, b, gap_open=2, gap=1) <= oracle.sw_score(a, b)
+
+
+def test_affine_random_len5_6_brute():
+    st = synth.Stream(2025, 5)
+    for _ in range(300):
+        la, lb = (int(v) for v in st.integers(5, 6, (2,)))
+        a = "".join("ACGT"[c] for c in synth.random_codes(st, (la,)))
+        b = "".join("ACGT"[c] for c in synth.random_codes(st, (lb,)))
+        assert oracle.sw_score_affine(a, b, gap_open=2, gap=1) == oracle.brute_score_affine(a, b, 2, 1)
+
+
+def test_distance_clamped_into_uint16_range():
+    # match +2 lets S exceed max(la, lb): the stored distance is clamped at 0
+    rs = synth.from_strings(["ACGTACGT", "ACGTACGT", "ACG"])
+    tri = oracle.all_pairs(rs, match=2, mismatch=-3, gap=1)
+    assert tri.tolist() == [0, 2, 2]                  # S = 16, 6, 6 against max = 8, 8, 8
+    assert oracle.all_pairs(rs).tolist() == [0, 5, 5]
