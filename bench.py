@@ -48,15 +48,21 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--mode", choices=["allpairs", "batch", "serve", "mds"], default="allpairs")
+    ap.add_argument("--mode", choices=["allpairs", "batch", "serve", "mds", "components", "affine"],
+                    default="allpairs")
     ap.add_argument("--serve-requests", type=int, default=40,
                     help="requests in the serving phase of the all-pairs run (0 = skip)")
     ap.add_argument("--serve-load", type=float, default=0.8,
                     help="offered load of that phase, as a fraction of measured pairs/s")
     ap.add_argument("--samples", type=int, default=64, help="batch mode: samples")
+    ap.add_argument("--small-requests", type=int, default=400,
+                    help="serve mode: requests of the small-request comparison")
     ap.add_argument("--mds-k", type=int, default=64, help="mds mode: sketch columns k")
     ap.add_argument("--mds-r", type=int, default=50, help="mds mode: coordinates r (paper: 50)")
     ap.add_argument("--mds-q", type=int, default=2, help="mds mode: subspace-iteration rounds")
+    ap.add_argument("--gap-open", type=int, default=2, help="affine mode: gap opening penalty")
+    ap.add_argument("--th", type=str, default="25/100",
+                    help="components mode: hit rule num/den (97 %% homology = 3/100) or an absolute d")
     return ap.parse_args(argv)
 
 
@@ -415,13 +421,13 @@ def percentile(xs, p):
 
 
 def serve_phase(gbd, ctx, ref_handle, ref_rs, dev, n_requests, load=1.0, capacity_pps=1.0,
-                seed=1005, check=True, burst=False):
+                seed=1005, check=True, burst=False, nq_hi=4096):
     """Poisson arrivals of query batches against a resident reference set; returns
     latency percentiles (submit -> rows complete) and served pairs/s.  The arrival rate
     makes the offered pairs/s of this very request sample `load` x `capacity_pps`."""
     import torch
     from paper_1803_02272_gb300 import synth
-    reqs = synth.workload_served_queries(n_requests, 1.0, seed=seed)   # arrivals at rate 1/s
+    reqs = synth.workload_served_queries(n_requests, 1.0, seed=seed, nq_hi=nq_hi)   # arrivals at rate 1/s
     n_ref = ref_rs.n
     mean_pairs = float(np.mean([r.reads.n for r in reqs])) * n_ref
     rate_per_s = load * capacity_pps / mean_pairs
@@ -547,10 +553,27 @@ def run_serve_mode(args):
     for load in (0.5, 0.8, 0.95):
         loads[str(load)] = serve_phase(gbd, ctx, ref, ref_rs, dev, args.serve_requests, load=load,
                                        capacity_pps=burst["pairs_per_s"], seed=2000 + int(load * 100))
+    # many small requests (1-16 reads each): per-request launch and set-up costs dominate a
+    # plain loop, and the server folds concurrent requests into shared launches
+    small = synth.workload_served_queries(args.small_requests, 1.0, seed=1007, nq_hi=16)
+    small_pairs = sum(r.reads.n for r in small) * ref_rs.n
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in small:
+        qh = ctx.load(r.reads)
+        ctx.tile(qh, 0, qh.n, ref, 0, ref.n, out=out.view(-1))
+    torch.cuda.synchronize()
+    small_plain_pps = small_pairs / (time.perf_counter() - t0)
+    small_burst = serve_phase(gbd, ctx, ref, ref_rs, dev, args.small_requests, seed=1007, check=True,
+                              burst=True, nq_hi=16)
     line = {"mode": "serve", "reference_reads": ref_rs.n, "requests": len(reqs),
             "plain_sequential_pairs_per_s": plain_pps, "server_burst": burst,
             "server_under_load": loads,
-            "server_vs_plain": burst["pairs_per_s"] / plain_pps}
+            "server_vs_plain": burst["pairs_per_s"] / plain_pps,
+            "small_requests": {"requests": len(small), "queries_per_request": "log-U[1,16]",
+                               "plain_sequential_pairs_per_s": small_plain_pps,
+                               "server_burst": small_burst,
+                               "server_vs_plain": small_burst["pairs_per_s"] / small_plain_pps}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -696,6 +719,160 @@ def run_mds_mode(args):
     return 0
 
 
+def run_components_mode(args):
+    """Threshold-graph components (section 5) of the paper-scale triangle: the streaming
+    pass over a computed triangle timed alone (HBM roofline), then the whole pipeline from
+    host reads to host labels."""
+    import torch
+    from paper_1803_02272_gb300 import gbd, synth
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    if "/" in args.th:
+        num, den = (int(x) for x in args.th.split("/"))
+        th = gbd.threshold(num, den, 65535)
+    else:
+        th = gbd.threshold(1, 1, int(args.th))
+    rs = synth.workload_paper_scale(n=args.n, len_lo=args.len_lo, len_hi=args.len_hi)
+    n = rs.n
+    m = n * (n - 1) // 2
+    ctx = gbd.Context(0)
+    s_h = ctx.load(rs)
+    tri = ctx.all_pairs(s_h)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    edges = torch.empty(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        gbd.gbd_tri_components(ctx.handle, s_h.handle, tri, th, labels, edges, stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    launches0 = gbd.gbd_kernel_launches()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gbd.gbd_tri_components(ctx.handle, s_h.handle, tri, th, labels, edges, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    launches = (gbd.gbd_kernel_launches() - launches0) // max(args.steps, 1)
+    clocks = sampler.stop()
+    t = float(np.mean(times))
+    lab = labels.cpu().numpy().astype(np.int64)
+    ne = int(edges.cpu().numpy()[0])
+    # sampled check against the oracle: every sampled hit pair shares a component; labels
+    # are roots (label[label[i]] == label[i] <= i)
+    import oracle
+    from oracle import threshold as oth
+    rng = np.random.default_rng(5)
+    i = rng.integers(0, n - 1, size=3000)
+    j = i + 1 + (rng.random(3000) * (n - 1 - i)).astype(np.int64)
+    d = oracle.pairs(rs, i, j)
+    L = rs.lengths
+    hit = oth.is_hit(d, L[i], L[j], th.num, th.den, th.abs_max)
+    check = {"pairs_checked": 3000, "hits": int(hit.sum()),
+             "hit_pairs_split": int(np.count_nonzero(hit & (lab[i] != lab[j]))),
+             "labels_are_roots": bool(np.all(lab[lab] == lab) and np.all(lab <= np.arange(n)))}
+    # whole pipeline through the C ABI with host buffers: reads in, labels out
+    seq_h = torch.from_numpy(rs.seq).pin_memory()
+    off_h = torch.from_numpy(rs.offsets.view(np.int64)).pin_memory()
+    lab_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sh = gbd.gbd_load_reads(ctx.handle, seq_h, off_h, n, stream)
+    gbd.gbd_threshold_components(ctx.handle, sh, th, labels, edges, None, stream)
+    lab_h.copy_(labels, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e = time.perf_counter() - t0
+    gbd.gbd_free_set(sh)
+    bytes_alg = m * 2 + n * 2 + n * 4 * 3
+    hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    line = {"metric": f"threshold-graph components of the n={n} triangle, rule {args.th}",
+            "value": t, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u16 distances, u32 labels", "data": "synthetic",
+            "config": {"workload": f"threshold graph (section 5) over the all-pairs triangle of {n} "
+                                   "paper-scale synthetic reads", "n_reads": n, "pairs": m,
+                       "rule": "d*den <= num*max(la,lb)" if "/" in args.th else "d <= theta",
+                       "l2": "10 GB triangle, larger than L2; 512 MiB flush between steps"},
+            "roofline": {"bound": "hbm", "achieved": bytes_alg / t / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": bytes_alg / t / 1e9 / hbm, "traffic": None,
+                         "kernel": "tri_union_kernel + iota/flatten (one gbd_tri_components call)",
+                         "peak_source": "of measured: MEASURED_PEAKS hbm_gbs (copy)"},
+            "components": int(len(np.unique(lab))), "edges": ne, "clocks": clocks,
+            "gpu_launches": int(launches), "spot_check": check,
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(rs.seq.nbytes + rs.offsets.nbytes),
+                    "d2h_bytes_per_step": int(n * 4), "note": "load + all-pairs + components, host labels"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# Affine recurrence per cell on the general kernel (int32, one cell per lane-op): E and F
+# (one add-max each), H (add-max against 0, then a 3-way max), the running maximum.
+AFFINE_OPS_PER_CELL = 5.0
+
+
+def run_affine_mode(args):
+    """Affine-gap scoring (Gotoh) on the general kernel: all pairs of a read set, exact
+    against the oracle on sampled pairs."""
+    import torch
+    from paper_1803_02272_gb300 import gbd, synth
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n = args.n
+    rs = synth.workload_paper_scale(n=n, len_lo=args.len_lo, len_hi=args.len_hi)
+    m = n * (n - 1) // 2
+    cells = float(rs.total_cells())
+    ctx = gbd.Context(0, gap_open=args.gap_open)
+    s_h = ctx.load(rs)
+    tri = torch.empty(m, dtype=torch.int16, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        gbd.gbd_all_pairs(ctx.handle, s_h.handle, tri, m, stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    launches0 = gbd.gbd_kernel_launches()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gbd.gbd_all_pairs(ctx.handle, s_h.handle, tri, m, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    launches = (gbd.gbd_kernel_launches() - launches0) // max(args.steps, 1)
+    clocks = sampler.stop()
+    import oracle
+    rng = np.random.default_rng(11)
+    i = rng.integers(0, n - 1, size=400)
+    j = i + 1 + (rng.random(400) * (n - 1 - i)).astype(np.int64)
+    idx = i * n - i * (i + 1) // 2 + (j - i - 1)
+    got = tri[torch.from_numpy(idx).to(dev)].cpu().numpy().view(np.uint16)
+    want = oracle.pairs(rs, i, j, gap_open=args.gap_open)
+    t = float(np.mean(times))
+    rate = max(gbd.gbd_probe_op_rate(gbd.PROBE_OPS.index(nm), 20000, stream)
+               for nm in ("VIMAX3_S16X2", "VIADDMAX_S16X2"))
+    peak = rate / AFFINE_OPS_PER_CELL / 1e9
+    line = {"metric": f"GCUPS, all-pairs n={n}, affine gaps (open {args.gap_open}, extend 1), exact",
+            "value": cells / t / 1e9, "unit": "GCUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic", "config": workload_config(rs),
+            "roofline": {"bound": "alu", "achieved": cells / t / 1e9, "peak": peak, "unit": "GCUPS",
+                         "frac": cells / t / 1e9 / peak, "traffic": None,
+                         "peak_source": "of measured: ALU-pipe issue rate (probe) x 1 cell / 5 ops (E, F, "
+                                        "H add-max and 3-way max, running max)"},
+            "clocks": clocks, "gpu_launches": int(launches),
+            "spot_check": {"pairs_checked": 400, "mismatches": int(np.count_nonzero(got != want))},
+            "e2e": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -706,6 +883,10 @@ def main(argv=None):
         return run_serve_mode(args)
     if args.mode == "mds":
         return run_mds_mode(args)
+    if args.mode == "components":
+        return run_components_mode(args)
+    if args.mode == "affine":
+        return run_affine_mode(args)
     return run_gbd(args)
 
 

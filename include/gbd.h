@@ -10,7 +10,7 @@
  * The paper fixes no scores and no score-to-distance rule.  This library's readings,
  * all of them fields of gbd_params:
  *   s(x,y) = +match if x == y else +mismatch (defaults +1 / -1); linear gap penalty
- *   `gap` per gapped base (default 1);
+ *   `gap` per gapped base (default 1), optionally affine (`gap_open` per gap run);
  *   H(i,0) = H(0,j) = 0, H(i,j) = max(0, H(i-1,j-1)+s(a_i,b_j), H(i-1,j)-gap,
  *   H(i,j-1)-gap), S = max over all cells of H;
  *   d = max(la, lb) - S (GBD_CONV_MAX, default), stored as uint16.
@@ -69,6 +69,9 @@ typedef struct {
     int32_t  kernel;      /* GBD_KERNEL_* (default GBD_KERNEL_AUTO) */
     uint64_t hbm_budget;  /* server admission budget in bytes; 0 = 90 % of free memory */
     uint32_t timeout_us;  /* bound on any host wait inside the library; 0 = 60 s */
+    int16_t  gap_open;    /* affine gaps (Gotoh): a run of L gapped bases costs
+                             gap_open + L * gap; 0 = linear (default).  > 0 runs on the
+                             general kernel. */
 } gbd_params;
 
 /* Fills *p with the defaults above. */
@@ -142,6 +145,49 @@ void gbd_server_destroy(gbd_server *srv);
 int gbd_tile_noalloc(gbd_ctx *ctx, const uint8_t *d_seqA, const uint64_t *d_offA, uint64_t nA,
                      const uint8_t *d_seqB, const uint64_t *d_offB, uint64_t nB,
                      uint32_t max_len, uint16_t *d_out, uint64_t ld, void *stream);
+
+/* ---------------------------------------------------------------- threshold epilogue
+ * A distance d between reads of lengths la, lb is a hit when
+ *   d <= abs_max  and  d * den <= num * max(la, lb)
+ * (integer arithmetic; the paper's 97 % homology gap of section 4.3 is num/den = 3/100
+ * with abs_max = 65535, the absolute threshold theta of section 5 is num = den = 1,
+ * abs_max = theta).  den must be positive. */
+typedef struct {
+    uint32_t num, den;
+    uint32_t abs_max;
+} gbd_threshold;
+
+/* Rectangle with the threshold applied as each distance is computed (section 4.3:
+ * sample reads against annotated reference reads).  Any of the outputs may be NULL:
+ *   d_out         the dense rectangle, as gbd_tile (ld >= b1-b0);
+ *   d_hits        up to hit_capacity hits as 3 uint32 each: row read index (in A), column
+ *                 read index (in B), d -- in no particular order; needs d_hit_count;
+ *   d_hit_count   (device, one uint64) the number of hits, also those past the capacity;
+ *                 zeroed by the call;
+ *   d_ref_labels  (device, int32 by B read index) species of the reference reads, < 0 for
+ *                 an unannotated read; with d_row_labels (device, a1-a0 int32, set by the
+ *                 call): the species shared by all hits of a row, -1 for no hit, -2 when
+ *                 the hits disagree (the diagno-syst rule of section 4.3).
+ * Asynchronous on `stream`.  EINVAL on bad ranges or a NULL d_hit_count with d_hits. */
+int gbd_tile_hits(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd_set *B,
+                  uint64_t b0, uint64_t b1, const gbd_threshold *th, uint16_t *d_out, uint64_t ld,
+                  uint32_t *d_hits, uint64_t hit_capacity, uint64_t *d_hit_count,
+                  const int32_t *d_ref_labels, int32_t *d_row_labels, void *stream);
+
+/* Connected components of the threshold graph of a read set (section 5: vertices are the
+ * reads, an edge joins i < j when the pair is a hit).  d_labels (device, n uint32):
+ * the smallest read index of each read's component.  d_edges (device, one uint64, may be
+ * NULL): the number of edges.  d_tri (may be NULL): the dense triangle as gbd_all_pairs,
+ * computed in the same pass.  The unions happen as the distances are computed; no edge
+ * list is stored.  Asynchronous on `stream`. */
+int gbd_threshold_components(gbd_ctx *ctx, const gbd_set *set, const gbd_threshold *th, uint32_t *d_labels,
+                             uint64_t *d_edges, uint16_t *d_tri, void *stream);
+
+/* The same components from a triangle already computed by gbd_all_pairs for this set
+ * (d_tri, n(n-1)/2 entries): one streaming pass, so several thresholds can be explored
+ * without recomputing distances. */
+int gbd_tri_components(gbd_ctx *ctx, const gbd_set *set, const uint16_t *d_tri, const gbd_threshold *th,
+                       uint32_t *d_labels, uint64_t *d_edges, void *stream);
 
 /* ---------------------------------------------------------------- MDS (paper sections 3 and 6.2)
  * Classical multidimensional scaling of the distance triangle: Torgerson's double

@@ -45,10 +45,14 @@ static bool is_device_pointer(const void *p)
 
 Scoring scoring_of(const gbd_ctx *ctx)
 {
-    return {ctx->params.match, ctx->params.mismatch, ctx->params.gap, ctx->params.conversion};
+    return {ctx->params.match, ctx->params.mismatch, ctx->params.gap, ctx->params.conversion,
+            ctx->params.gap_open};
 }
 
-static bool default_scores(const gbd_params &p) { return p.match == 1 && p.mismatch == -1 && p.gap == 1; }
+static bool default_scores(const gbd_params &p)
+{
+    return p.match == 1 && p.mismatch == -1 && p.gap == 1 && p.gap_open == 0;
+}
 
 // The systolic kernel is specialised to the default scores.
 static bool use_systolic(const gbd_ctx *ctx)
@@ -136,6 +140,75 @@ static int all_pairs_systolic(gbd_ctx *ctx, gbd_set *set, uint16_t *d_tri, cudaS
     cudaFreeAsync(d_job, st);
     if (rc != GBD_OK) return rc;
     return long_rows_general(ctx, set, d_tri, st);
+}
+
+// All pairs of one set into the dense triangle.
+static int all_pairs_impl(gbd_ctx *ctx, const gbd_set *set, uint16_t *d_tri, cudaStream_t st)
+{
+    if (use_systolic(ctx)) return all_pairs_systolic(ctx, const_cast<gbd_set *>(set), d_tri, st);
+    const uint64_t n = set->n;
+    GeneralJob job{set->view(), set->view(), 0, n, 0, n, 0, OUT_TRI, d_tri};
+    return run_general(job, scoring_of(ctx), ctx->sm_count, st);
+}
+
+// Rectangle A[a0,a1) x B[b0,b1) into d_out (leading dimension ld).
+static int tile_impl(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd_set *B,
+                     uint64_t b0, uint64_t b1, uint16_t *d_out, uint64_t ld, cudaStream_t st)
+{
+    if (!use_systolic(ctx)) {
+        GeneralJob job{A->view(), B->view(), a0, a1, b0, b1, ld, OUT_RECT, d_out};
+        return run_general(job, scoring_of(ctx), ctx->sm_count, st);
+    }
+    std::vector<SysEntry> entries;
+    std::vector<uint8_t> rows;
+    std::vector<uint32_t> long_rows;
+    for (uint64_t r = a0; r < a1; ++r) {
+        if (A->h_len[r] <= kSystolicMaxQuery) {
+            entries.push_back({0u, (uint32_t)r, (uint32_t)b0, (uint32_t)(b1 - b0)});
+            rows.push_back((uint8_t)systolic_rows(A->h_len[r]));
+        } else {
+            long_rows.push_back((uint32_t)r);
+        }
+    }
+    int rc = GBD_OK;
+    if (!entries.empty()) {
+        SysJob job{};
+        job.Q = A->view();
+        job.S = B->view();
+        job.sub_perm = nullptr;
+        job.out = d_out;
+        job.ld = ld;
+        job.row0 = a0;
+        job.col0 = b0;
+        job.mode = OUT_RECT;
+        job.conversion = ctx->params.conversion;
+        SysJob *d_job = nullptr;
+        SysPlan plan;
+        if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
+        if ((rc = build_plan(entries, rows, plan, false, st, 0, B->mean_len, ctx->sm_count)) != GBD_OK)
+            return rc;
+        rc = run_systolic(d_job, plan, ctx->sm_count, st, ctx->aux, ctx->fork, ctx->join);
+        cudaFreeAsync(d_job, st);
+        free_plan(plan, st);
+        if (rc != GBD_OK) return rc;
+    }
+    if (!long_rows.empty()) {
+        uint32_t *d_rows = nullptr;
+        if ((rc = upload(long_rows.data(), long_rows.size(), &d_rows, st)) != GBD_OK) return rc;
+        GeneralJob gj{A->view(), B->view(), a0, a1, b0, b1, ld, OUT_RECT, d_out};
+        gj.rows = d_rows;
+        gj.nrows = long_rows.size();
+        rc = run_general(gj, scoring_of(ctx), ctx->sm_count, st);
+        cudaFreeAsync(d_rows, st);
+    }
+    return rc;
+}
+
+static int check_threshold(const gbd_threshold *th)
+{
+    if (!th) return fail(GBD_EINVAL, "NULL threshold");
+    if (th->den == 0) return fail(GBD_EINVAL, "threshold den must be positive");
+    return GBD_OK;
 }
 
 
@@ -266,6 +339,7 @@ int gbd_create(gbd_ctx **out, int device, const gbd_params *p)
     gbd_default_params(&prm);
     if (p) prm = *p;
     if (prm.gap < 0) return fail(GBD_EINVAL, "gbd_create: gap penalty must be >= 0");
+    if (prm.gap_open < 0) return fail(GBD_EINVAL, "gbd_create: gap opening penalty must be >= 0");
     if (prm.conversion < GBD_CONV_MAX || prm.conversion > GBD_CONV_SCORE)
         return fail(GBD_EINVAL, "gbd_create: unknown conversion");
     if (prm.kernel < GBD_KERNEL_AUTO || prm.kernel > GBD_KERNEL_SYSTOLIC)
@@ -439,10 +513,7 @@ int gbd_all_pairs(gbd_ctx *ctx, const gbd_set *set, uint16_t *d_tri, uint64_t tr
     if (need == 0) return GBD_OK;
     if (!d_tri) return fail(GBD_EINVAL, "gbd_all_pairs: d_tri is NULL");
     GBD_CUDA_TRY(cudaSetDevice(ctx->device));
-    if (use_systolic(ctx))
-        return all_pairs_systolic(ctx, const_cast<gbd_set *>(set), d_tri, (cudaStream_t)stream);
-    GeneralJob job{set->view(), set->view(), 0, n, 0, n, 0, OUT_TRI, d_tri};
-    return run_general(job, scoring_of(ctx), ctx->sm_count, (cudaStream_t)stream);
+    return all_pairs_impl(ctx, set, d_tri, (cudaStream_t)stream);
 }
 
 int gbd_tile(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd_set *B,
@@ -455,54 +526,85 @@ int gbd_tile(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd
     if (a0 == a1 || b0 == b1) return GBD_OK;
     if (!d_out) return fail(GBD_EINVAL, "gbd_tile: d_out is NULL");
     GBD_CUDA_TRY(cudaSetDevice(ctx->device));
+    return tile_impl(ctx, A, a0, a1, B, b0, b1, d_out, ld, (cudaStream_t)stream);
+}
+
+int gbd_tile_hits(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd_set *B,
+                  uint64_t b0, uint64_t b1, const gbd_threshold *th, uint16_t *d_out, uint64_t ld,
+                  uint32_t *d_hits, uint64_t hit_capacity, uint64_t *d_hit_count,
+                  const int32_t *d_ref_labels, int32_t *d_row_labels, void *stream)
+{
+    if (!ctx || !A || !B) return fail(GBD_EINVAL, "gbd_tile_hits: NULL context or set");
+    int rc = check_threshold(th);
+    if (rc != GBD_OK) return rc;
+    if (a0 > a1 || a1 > A->n || b0 > b1 || b1 > B->n)
+        return fail(GBD_EINVAL, "gbd_tile_hits: row or column range outside the sets");
+    if (d_out && ld < b1 - b0) return fail(GBD_EINVAL, "gbd_tile_hits: ld is smaller than the column count");
+    if (d_hits && !d_hit_count) return fail(GBD_EINVAL, "gbd_tile_hits: a hit list needs d_hit_count");
+    if ((d_ref_labels == nullptr) != (d_row_labels == nullptr))
+        return fail(GBD_EINVAL, "gbd_tile_hits: annotation needs both d_ref_labels and d_row_labels");
+    if (a1 > 0xffffffffull || b1 > 0xffffffffull) return fail(GBD_EINVAL, "gbd_tile_hits: read index beyond 32 bits");
+    GBD_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
-    if (!use_systolic(ctx)) {
-        GeneralJob job{A->view(), B->view(), a0, a1, b0, b1, ld, OUT_RECT, d_out};
-        return run_general(job, scoring_of(ctx), ctx->sm_count, st);
+    if (d_hit_count) GBD_CUDA_TRY(cudaMemsetAsync(d_hit_count, 0, sizeof(uint64_t), st));
+    if (d_row_labels && a1 > a0) GBD_CUDA_TRY(cudaMemsetAsync(d_row_labels, 0xff, (a1 - a0) * sizeof(int32_t), st));
+    if (a0 == a1 || b0 == b1) return GBD_OK;
+    // distances first (into the caller's rectangle or a scratch one), then the epilogue
+    // streams over them
+    uint16_t *rect = d_out;
+    uint64_t rld = ld;
+    if (!rect) {
+        rld = b1 - b0;
+        GBD_CUDA_TRY(cudaMallocAsync((void **)&rect, (a1 - a0) * rld * sizeof(uint16_t), st));
     }
-    std::vector<SysEntry> entries;
-    std::vector<uint8_t> rows;
-    std::vector<uint32_t> long_rows;
-    for (uint64_t r = a0; r < a1; ++r) {
-        if (A->h_len[r] <= kSystolicMaxQuery) {
-            entries.push_back({0u, (uint32_t)r, (uint32_t)b0, (uint32_t)(b1 - b0)});
-            rows.push_back((uint8_t)systolic_rows(A->h_len[r]));
-        } else {
-            long_rows.push_back((uint32_t)r);
-        }
-    }
-    int rc = GBD_OK;
-    if (!entries.empty()) {
-        SysJob job{};
-        job.Q = A->view();
-        job.S = B->view();
-        job.sub_perm = nullptr;
-        job.out = d_out;
-        job.ld = ld;
-        job.row0 = a0;
-        job.col0 = b0;
-        job.mode = OUT_RECT;
-        job.conversion = ctx->params.conversion;
-        SysJob *d_job = nullptr;
-        SysPlan plan;
-        if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
-        if ((rc = build_plan(entries, rows, plan, false, st, 0, B->mean_len, ctx->sm_count)) != GBD_OK)
-            return rc;
-        rc = run_systolic(d_job, plan, ctx->sm_count, st, ctx->aux, ctx->fork, ctx->join);
-        cudaFreeAsync(d_job, st);
-        free_plan(plan, st);
-        if (rc != GBD_OK) return rc;
-    }
-    if (!long_rows.empty()) {
-        uint32_t *d_rows = nullptr;
-        if ((rc = upload(long_rows.data(), long_rows.size(), &d_rows, st)) != GBD_OK) return rc;
-        GeneralJob gj{A->view(), B->view(), a0, a1, b0, b1, ld, OUT_RECT, d_out};
-        gj.rows = d_rows;
-        gj.nrows = long_rows.size();
-        rc = run_general(gj, scoring_of(ctx), ctx->sm_count, st);
-        cudaFreeAsync(d_rows, st);
-    }
+    rc = tile_impl(ctx, A, a0, a1, B, b0, b1, rect, rld, st);
+    if (rc == GBD_OK)
+        rc = launch_rect_epilogue(rect, rld, A->view(), a0, a1, B->view(), b0, b1, Threshold{th->num, th->den, th->abs_max},
+                                  d_hits, d_hits ? hit_capacity : 0,
+                                  reinterpret_cast<unsigned long long *>(d_hit_count), d_ref_labels, d_row_labels,
+                                  ctx->sm_count, st);
+    if (!d_out) cudaFreeAsync(rect, st);
     return rc;
+}
+
+int gbd_threshold_components(gbd_ctx *ctx, const gbd_set *set, const gbd_threshold *th, uint32_t *d_labels,
+                             uint64_t *d_edges, uint16_t *d_tri, void *stream)
+{
+    if (!ctx || !set || !d_labels) return fail(GBD_EINVAL, "gbd_threshold_components: NULL argument");
+    int rc = check_threshold(th);
+    if (rc != GBD_OK) return rc;
+    const uint64_t n = set->n;
+    if (n > 0xffffffffull) return fail(GBD_EINVAL, "gbd_threshold_components: more than 2^32 reads");
+    GBD_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (d_edges) GBD_CUDA_TRY(cudaMemsetAsync(d_edges, 0, sizeof(uint64_t), st));
+    if (n == 0) return GBD_OK;
+    const uint64_t m = n * (n - 1) / 2;
+    uint16_t *tri = d_tri;
+    if (!tri && m > 0) GBD_CUDA_TRY(cudaMallocAsync((void **)&tri, m * sizeof(uint16_t), st));
+    if (m > 0) rc = all_pairs_impl(ctx, set, tri, st);
+    if (rc == GBD_OK)
+        rc = launch_tri_components(tri, set->view(), Threshold{th->num, th->den, th->abs_max}, d_labels,
+                                   reinterpret_cast<unsigned long long *>(d_edges), ctx->sm_count, st);
+    if (!d_tri && tri) cudaFreeAsync(tri, st);
+    return rc;
+}
+
+int gbd_tri_components(gbd_ctx *ctx, const gbd_set *set, const uint16_t *d_tri, const gbd_threshold *th,
+                       uint32_t *d_labels, uint64_t *d_edges, void *stream)
+{
+    if (!ctx || !set || !d_labels) return fail(GBD_EINVAL, "gbd_tri_components: NULL argument");
+    int rc = check_threshold(th);
+    if (rc != GBD_OK) return rc;
+    const uint64_t n = set->n;
+    if (n >= 2 && !d_tri) return fail(GBD_EINVAL, "gbd_tri_components: NULL triangle");
+    if (n > 0xffffffffull) return fail(GBD_EINVAL, "gbd_tri_components: more than 2^32 reads");
+    GBD_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (d_edges) GBD_CUDA_TRY(cudaMemsetAsync(d_edges, 0, sizeof(uint64_t), st));
+    if (n == 0) return GBD_OK;
+    return launch_tri_components(d_tri, set->view(), Threshold{th->num, th->den, th->abs_max}, d_labels,
+                                 reinterpret_cast<unsigned long long *>(d_edges), ctx->sm_count, st);
 }
 
 int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns, uint16_t *const *d_tris,

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -115,6 +116,7 @@ enum OutMode : int { OUT_TRI = 0, OUT_RECT = 1, OUT_TRI_ROWS = 2 };
 
 struct Scoring {
     int match, mismatch, gap, conversion;
+    int gap_open = 0;           // > 0: affine gaps (Gotoh), gap run of L costs gap_open + L*gap
 };
 
 // General kernel: one pair per thread, int32 strip DP, boundary rows in scratch.
@@ -133,6 +135,23 @@ int run_general(const GeneralJob &job, const Scoring &sc, int sm_count, cudaStre
 // (scratch_ints ints); allocates nothing.
 int run_general_in(const GeneralJob &job, const Scoring &sc, int *scratch, uint64_t scratch_ints,
                    int sm_count, cudaStream_t stream);
+
+// Threshold epilogue (threshold.cu), streaming over distances already computed.
+struct Threshold {
+    uint32_t num, den, abs_max;
+};
+// Rectangle D[r][c] = out[(r-a0)*ld + (c-b0)], r in [a0,a1), c in [b0,b1): hits appended
+// to hits (3 words each, up to cap; every hit counted in *count), and row annotation
+// from col_labels into row_labels (by r - a0) when both are set.
+int launch_rect_epilogue(const uint16_t *out, uint64_t ld, const DeviceReads &A, uint64_t a0, uint64_t a1,
+                         const DeviceReads &B, uint64_t b0, uint64_t b1, const Threshold &th, uint32_t *hits,
+                         uint64_t cap, unsigned long long *count, const int32_t *col_labels,
+                         int32_t *row_labels, int sm_count, cudaStream_t st);
+// Triangle of a set: every hit pair (i, j) is joined in the union-find forest `parent`
+// (which starts as parent[i] = i) and counted in *count (if set); then every read is
+// pointed at its root, the smallest read of its component.
+int launch_tri_components(const uint16_t *tri, const DeviceReads &S, const Threshold &th, uint32_t *parent,
+                          unsigned long long *count, int sm_count, cudaStream_t st);
 
 // Frees the context's cached batch graph.
 void free_batch_cache(gbd_ctx *ctx);

@@ -10,9 +10,8 @@
 //                         (mds_gemm.cu), slice sum, column means of the product, and
 //                         Y = -2^(s-1) (P - 1 mean^T); J W J X = J W (J X) needs no
 //                         centred copy of W
-//   orthonormalise        Gram S = Y^T Y (float64), S = V diag(s) V^T by cyclic Jacobi,
-//                         Q = Y V diag(s^-1/2) (directions with s below a floor dropped),
-//                         twice
+//   orthonormalise        Gram S = Y^T Y (float64), Cholesky S = R^T R, Q = Y R^-1
+//                         (columns whose pivot falls below a floor dropped), twice
 //   eigenpairs of B       B = Q^T (G Q) by the same Gram kernel, Jacobi, eigenvalues
 //                         sorted down, coordinates Q V_r diag(max(lambda, 0)^1/2)
 // All reductions run in a fixed order, so results do not depend on scheduling.
@@ -66,26 +65,67 @@ __device__ __forceinline__ uint16_t sq_half(uint32_t d, float scale)
 }
 
 // Tile (I, J), I <= J, of the square: W[I-block][J-block] from the triangle, and its
-// transpose W[J-block][I-block] through shared memory.
+// transpose W[J-block][I-block] through shared memory.  Off-diagonal tiles whose columns
+// all lie below n (all but a thin margin) take the fast path: each warp handles whole
+// 64-column row segments, one aligned 32-bit load per lane (the segment's parity fixed up
+// with a shuffle), 128-byte stores; the rest go element by element.
 __global__ void __launch_bounds__(256)
 sqdist_square_kernel(const uint16_t *__restrict__ tri, uint64_t n, uint64_t ld, float scale,
-                     uint16_t *__restrict__ W, uint64_t ntiles)
+                     uint16_t *__restrict__ W, uint64_t ntiles, int aligned)
 {
     __shared__ uint16_t t[ST][ST + 2];
     const uint64_t T = ld / ST;
     const uint64_t lin = blockIdx.x;
     if (lin >= ntiles) return;
-    // row I of the tile triangle holds T - I tiles
-    const double b = 2.0 * (double)T + 1.0;
-    int64_t I = (int64_t)((b - sqrt(fmax(b * b - 8.0 * (double)lin, 0.0))) * 0.5);
+    // row I of the tile triangle holds T - I tiles (float estimate, then exact fix-up)
+    const float b = 2.0f * (float)T + 1.0f;
+    int64_t I = (int64_t)((b - sqrtf(fmaxf(b * b - 8.0f * (float)lin, 0.0f))) * 0.5f);
     auto row_start = [&](int64_t r) { return (uint64_t)r * T - (uint64_t)r * (uint64_t)(r - 1) / 2; };
     if (I < 0) I = 0;
     while (I > 0 && row_start(I) > lin) --I;
     while ((uint64_t)(I + 1) < T && row_start(I + 1) <= lin) ++I;
     const uint64_t J = (uint64_t)I + (lin - row_start(I));
     const uint64_t i0 = (uint64_t)I * ST, j0 = J * ST;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // each thread: 4 consecutive columns of one row, 4 passes of 16 rows
+    const bool fast = aligned && (uint64_t)I != J && j0 + ST <= n;
+    if (fast) {
+        // every row i of this tile is below j0 < n, and its 64 columns lie in one
+        // triangle row: issue the eight rows' loads of this warp before using any
+        const uint32_t *tw = reinterpret_cast<const uint32_t *>(tri);
+        uint32_t lo[8], ex[8], odd[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint64_t k0 = tri_index(i0 + warp + 8 * q, j0, n);   // element 0 of the segment
+            const uint64_t w0 = k0 >> 1;
+            odd[q] = (uint32_t)(k0 & 1);
+            lo[q] = __ldg(tw + w0 + lane);
+            // for an odd start, lane 31 also needs the word after the segment's 32
+            ex[q] = (lane == 31 && odd[q]) ? __ldg(tw + w0 + 32) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int r = warp + 8 * q;
+            uint32_t hi = __shfl_down_sync(0xffffffffu, lo[q], 1);     // the next lane's word
+            if (lane == 31) hi = ex[q];
+            const uint32_t pair = odd[q] ? __funnelshift_r(lo[q], hi, 16) : lo[q];
+            const uint32_t pk =
+                (uint32_t)sq_half(pair & 0xffffu, scale) | ((uint32_t)sq_half(pair >> 16, scale) << 16);
+            t[r][2 * lane] = (uint16_t)(pk & 0xffffu);
+            t[r][2 * lane + 1] = (uint16_t)(pk >> 16);
+            *reinterpret_cast<uint32_t *>(W + (i0 + r) * ld + j0 + 2 * lane) = pk;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int r = warp + 8 * q;
+            const uint32_t pk = (uint32_t)t[2 * lane][r] | ((uint32_t)t[2 * lane + 1][r] << 16);
+            *reinterpret_cast<uint32_t *>(W + (j0 + r) * ld + i0 + 2 * lane) = pk;
+        }
+        return;
+    }
+
+    // general path: each thread 4 consecutive columns of one row, 4 passes of 16 rows
     const int c4 = (threadIdx.x & 15) * 4;
     for (int r = threadIdx.x >> 4; r < ST; r += 16) {
         const uint64_t i = i0 + r;
@@ -189,46 +229,58 @@ __global__ void center_scale_kernel(const float *__restrict__ P, const double *_
 // ------------------------------------------------------------------ A^T B in float64
 constexpr int kGramRows = 32;
 
-// partial[b] = sum over block b's rows of A[i]^T B[i] (k x k, float64 products of the
-// float32 inputs, exact), in a fixed order.
+// partial[b] = sum over block b's rows of A[i]^T B[i] (k x k), float64 products of the
+// float32 inputs (exact) summed in a fixed order.  Rows are staged in shared memory as
+// float64; each thread owns 4 x 4 tiles of the output in registers.
 __global__ void __launch_bounds__(256)
 xty_partial_kernel(const float *__restrict__ A, const float *__restrict__ B, uint64_t n, uint32_t k,
                    double *partial)
 {
-    extern __shared__ float sm[];
-    float *As = sm;                       // [kGramRows][k]
-    float *Bs = sm + kGramRows * k;       // [kGramRows][k]
+    extern __shared__ double smd[];
+    double *As = smd;                       // [kGramRows][k]
+    double *Bs = smd + kGramRows * k;       // [kGramRows][k]
     const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
     const uint64_t r0 = blockIdx.x * per, r1 = std::min<uint64_t>(n, r0 + per);
-    const uint32_t kk = k * k;
-    double *out = partial + (uint64_t)blockIdx.x * kk;
-    for (uint32_t o0 = 0; o0 < kk; o0 += blockDim.x * 16) {
-        double acc[16];
+    const uint32_t kt = k / 4;              // 4 x 4 tiles per side
+    const uint32_t ntiles = kt * kt;
+    double *out = partial + (uint64_t)blockIdx.x * k * k;
+    for (uint32_t t0 = 0; t0 < ntiles; t0 += blockDim.x) {
+        const uint32_t t = t0 + threadIdx.x;
+        const bool active = t < ntiles;
+        const uint32_t a0 = active ? (t / kt) * 4 : 0, b0 = active ? (t % kt) * 4 : 0;
+        double acc[4][4];
 #pragma unroll
-        for (int t = 0; t < 16; ++t) acc[t] = 0.0;
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[x][y] = 0.0;
         for (uint64_t rb = r0; rb < r1; rb += kGramRows) {
             const uint32_t rows = (uint32_t)std::min<uint64_t>(kGramRows, r1 - rb);
             __syncthreads();
             for (uint32_t e = threadIdx.x; e < rows * k; e += blockDim.x) {
-                As[e] = A[rb * k + e];
-                Bs[e] = B[rb * k + e];
+                As[e] = (double)A[rb * k + e];
+                Bs[e] = (double)B[rb * k + e];
             }
             __syncthreads();
+            if (active) {
+                for (uint32_t r = 0; r < rows; ++r) {
+                    const double2 a01 = *reinterpret_cast<const double2 *>(As + r * k + a0);
+                    const double2 a23 = *reinterpret_cast<const double2 *>(As + r * k + a0 + 2);
+                    const double2 b01 = *reinterpret_cast<const double2 *>(Bs + r * k + b0);
+                    const double2 b23 = *reinterpret_cast<const double2 *>(Bs + r * k + b0 + 2);
+                    const double av[4] = {a01.x, a01.y, a23.x, a23.y};
+                    const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
 #pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                const uint32_t o = o0 + threadIdx.x + t * blockDim.x;
-                if (o < kk) {
-                    const uint32_t a = o / k, b = o % k;
-                    double s = acc[t];
-                    for (uint32_t r = 0; r < rows; ++r) s += (double)As[r * k + a] * (double)Bs[r * k + b];
-                    acc[t] = s;
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
                 }
             }
         }
+        if (active) {
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            const uint32_t o = o0 + threadIdx.x + t * blockDim.x;
-            if (o < kk) out[o] = acc[t];
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) out[(a0 + x) * k + b0 + y] = acc[x][y];
         }
     }
 }
@@ -240,6 +292,68 @@ __global__ void xty_final_kernel(const double *__restrict__ partial, uint32_t np
         for (uint32_t b = 0; b < nparts; ++b) s += partial[(uint64_t)b * kk + o];
         C[o] = s;
     }
+}
+
+// ------------------------------------------------------------------ Cholesky QR step
+// S = Y^T Y = R^T R (R upper triangular), float64, one block; T = R^-1 (float32) so that
+// Q = Y T has orthonormal columns.  A column whose remaining pivot falls below
+// floor_rel * max diag(S) lies (numerically) in the span of the earlier columns: its row
+// of R and its column of T are set to 0, so Q gets a zero column there.
+__global__ void __launch_bounds__(256)
+chol_inverse_kernel(const double *__restrict__ S_in, uint32_t k, double floor_rel, float *__restrict__ T,
+                    uint32_t *flags)
+{
+    extern __shared__ double sc[];
+    double *R = sc;                 // k x k, becomes R (upper part)
+    double *Ti = sc + k * k;        // k x k, R^-1
+    __shared__ double smax;
+    __shared__ int keep[128];
+    const uint32_t kk = k * k;
+    for (uint32_t e = threadIdx.x; e < kk; e += blockDim.x) {
+        const uint32_t i = e / k, j = e % k;
+        const double a = 0.5 * (S_in[i * k + j] + S_in[j * k + i]);
+        R[e] = a;
+        Ti[e] = 0.0;
+        if (!isfinite(a)) atomicOr(flags, 2u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (uint32_t j = 0; j < k; ++j) m = fmax(m, R[j * k + j]);
+        smax = m;
+    }
+    __syncthreads();
+    // right-looking Cholesky on the upper triangle
+    for (uint32_t j = 0; j < k; ++j) {
+        const double d = R[j * k + j];
+        const bool ok = d > floor_rel * smax && d > 0.0;
+        const double rjj = ok ? sqrt(d) : 0.0;
+        __syncthreads();
+        for (uint32_t c = j + threadIdx.x; c < k; c += blockDim.x)
+            R[j * k + c] = ok ? (c == j ? rjj : R[j * k + c] / rjj) : 0.0;
+        if (threadIdx.x == 0) keep[j] = ok;
+        __syncthreads();
+        // trailing update A[r][c] -= R[j][r] R[j][c], j < r <= c
+        const uint32_t m = k - 1 - j;
+        for (uint32_t e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const uint32_t r = j + 1 + e / m, c = j + 1 + e % m;
+            if (c >= r) R[r * k + c] -= R[j * k + r] * R[j * k + c];
+        }
+        __syncthreads();
+    }
+    // T = R^-1 column by column (back substitution; dropped rows stay 0)
+    for (uint32_t c = threadIdx.x; c < k; c += blockDim.x) {
+        if (!keep[c]) continue;
+        Ti[c * k + c] = 1.0 / R[c * k + c];
+        for (int i = (int)c - 1; i >= 0; --i) {
+            if (!keep[i]) continue;
+            double s = 0.0;
+            for (uint32_t m2 = (uint32_t)i + 1; m2 <= c; ++m2) s += R[i * k + m2] * Ti[m2 * k + c];
+            Ti[i * k + c] = -s / R[i * k + i];
+        }
+    }
+    __syncthreads();
+    for (uint32_t e = threadIdx.x; e < kk; e += blockDim.x) T[e] = (float)Ti[e];
 }
 
 // ------------------------------------------------------------------ symmetric eigensolver
@@ -503,7 +617,7 @@ int gram_apply_in(const uint16_t *W, int32_t shift, const float *X, float *Y, Md
 
 int xty(const float *A, const float *B, MdsWork &w)
 {
-    const size_t smem = 2 * (size_t)kGramRows * w.k * sizeof(float);
+    const size_t smem = 2 * (size_t)kGramRows * w.k * sizeof(double);
     xty_partial_kernel<<<w.gram_blocks, 256, smem, w.st>>>(A, B, w.n, w.k, w.gram_part);
     GBD_LAUNCH_CHECK("xty_partial_kernel");
     xty_final_kernel<<<(w.k * w.k + 255) / 256, 256, 0, w.st>>>(w.gram_part, w.gram_blocks, w.k * w.k, w.gram);
@@ -521,7 +635,7 @@ int apply(const float *A, const float *T, uint32_t m, float *Out, MdsWork &w)
     return GBD_OK;
 }
 
-// Q = orthonormal basis of the range of Y (two eigen-based passes).  Y is overwritten.
+// Q = orthonormal basis of the range of Y (Cholesky QR, twice).  Y is overwritten.
 constexpr double kOrthFloor = 1e-12;
 
 int orthonormalise(float *Y, float *Q, MdsWork &w)
@@ -530,8 +644,8 @@ int orthonormalise(float *Y, float *Q, MdsWork &w)
     for (int pass = 0; pass < 2; ++pass) {
         int rc = xty(src, src, w);
         if (rc != GBD_OK) return rc;
-        jacobi_kernel<<<1, 256, jacobi_smem(w.k), w.st>>>(w.gram, w.k, 0, 0, kOrthFloor, w.T, nullptr, w.flags + 1);
-        GBD_LAUNCH_CHECK("jacobi_kernel");
+        chol_inverse_kernel<<<1, 256, jacobi_smem(w.k), w.st>>>(w.gram, w.k, kOrthFloor, w.T, w.flags + 1);
+        GBD_LAUNCH_CHECK("chol_inverse_kernel");
         rc = apply(src, w.T, w.k, dst, w);
         if (rc != GBD_OK) return rc;
         std::swap(src, dst);
@@ -551,7 +665,9 @@ int configure_kernels()
     GBD_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)jacobi_smem(kMaxJacobiK)));
     GBD_CUDA_TRY(cudaFuncSetAttribute(xty_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(2 * kGramRows * kMaxJacobiK * sizeof(float))));
+                                      (int)(2 * kGramRows * kMaxJacobiK * sizeof(double))));
+    GBD_CUDA_TRY(cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)jacobi_smem(kMaxJacobiK)));
     GBD_CUDA_TRY(cudaFuncSetAttribute(
         apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
         (int)((64 * (kMaxJacobiK + 1) + kMaxJacobiK * kMaxJacobiK) * sizeof(float))));
@@ -591,7 +707,9 @@ int sqdist_square_impl(gbd_ctx *ctx, const uint16_t *d_tri, uint64_t n, uint16_t
     const uint64_t T = ld / ST;
     const uint64_t ntiles = T * (T + 1) / 2;
     if (ntiles > 0x7fffffffull) return fail(GBD_EINVAL, "square too large");
-    sqdist_square_kernel<<<(unsigned)ntiles, 256, 0, st>>>(d_tri, n, ld, (float)std::ldexp(1.0, -s), d_w, ntiles);
+    const int aligned = (reinterpret_cast<uintptr_t>(d_tri) % 4) == 0 ? 1 : 0;
+    sqdist_square_kernel<<<(unsigned)ntiles, 256, 0, st>>>(d_tri, n, ld, (float)std::ldexp(1.0, -s), d_w, ntiles,
+                                                            aligned);
     GBD_LAUNCH_CHECK("sqdist_square_kernel");
     return GBD_OK;
 }

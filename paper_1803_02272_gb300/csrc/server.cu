@@ -107,7 +107,7 @@ bool valid_base(uint8_t c)
 
 bool use_systolic_scores(const gbd_params &p)
 {
-    return p.kernel != GBD_KERNEL_GENERAL && p.match == 1 && p.mismatch == -1 && p.gap == 1;
+    return p.kernel != GBD_KERNEL_GENERAL && p.match == 1 && p.mismatch == -1 && p.gap == 1 && p.gap_open == 0;
 }
 
 // Called with srv->mu held: one chunk of r finished (or failed with `err`).
@@ -238,7 +238,8 @@ std::string launch_batch(gbd_server *srv, const std::vector<Piece> &pieces, cuda
     }
     if (cudaEventRecord(uploaded, up) != cudaSuccess || cudaStreamWaitEvent(st, uploaded, 0) != cudaSuccess)
         err = "upload event failed";
-    const Scoring sc{ctx->params.match, ctx->params.mismatch, ctx->params.gap, ctx->params.conversion};
+    const Scoring sc{ctx->params.match, ctx->params.mismatch, ctx->params.gap, ctx->params.conversion,
+                     ctx->params.gap_open};
     for (const GeneralJob &gj : general)
         if (err.empty() && run_general(gj, sc, ctx->sm_count, st) != GBD_OK) err = gbd_last_error();
     if (err.empty() && !entries.empty() && run_systolic(d_jobs, plan, ctx->sm_count, st) != GBD_OK)

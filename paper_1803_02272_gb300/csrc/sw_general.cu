@@ -1,7 +1,8 @@
 // General pair kernel: one read pair per thread, any lengths (<= 65535), any scores.
 //
 // Smith-Waterman local score (paper section 2.2) by the textbook recurrence
-//   H(i,j) = max(0, H(i-1,j-1) + s(a_i,b_j), H(i-1,j) - gap, H(i,j-1) - gap),
+//   H(i,j) = max(0, H(i-1,j-1) + s(a_i,b_j), H(i-1,j) - gap, H(i,j-1) - gap)
+// (or its affine-gap form, below),
 // S = max H, converted to a distance in the epilogue.  The query read is swept in
 // strips of R rows held in registers; the strip's last row is handed to the next
 // strip through a per-thread boundary row in scratch memory, laid out column-major
@@ -52,13 +53,22 @@ __device__ __forceinline__ uint16_t convert(int S, int la, int lb, int conversio
     return (uint16_t)d;
 }
 
+// Linear gaps: H = max(0, H_d + s, H_u - gap, H_l - gap).  Affine gaps (Gotoh): E carries
+// a horizontal gap run along the strip's rows, F a vertical one down the column (across
+// strips through a second boundary row), H = max(0, H_d + s, E, F) with
+// E = max(E_l - gap, H_l - gap_open - gap), F = max(F_u - gap, H_u - gap_open - gap).
+template <bool AFFINE>
 __global__ void __launch_bounds__(128)
 sw_general_kernel(GeneralJob job, Scoring sc, int *__restrict__ scratch, uint64_t units)
 {
+    constexpr int NEG = -(1 << 28);
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
     int *bnd = scratch + tid;                       // bnd[j * nthr] = H(strip top - 1, j)
+    // affine: F(strip top - 1, j) in the second half of the scratch
+    int *bndf = scratch + (uint64_t)(job.B.stride * kBasesPerWord + 1) * nthr + tid;
     const uint64_t nb = job.b1 - job.b0;
+    const int goe = sc.gap_open + sc.gap;
 
     for (uint64_t u = tid; u < units; u += nthr) {
         uint64_t ia, jb, o;
@@ -90,27 +100,38 @@ sw_general_kernel(GeneralJob job, Scoring sc, int *__restrict__ scratch, uint64_
             uint32_t ac[kStrip];
 #pragma unroll
             for (int r = 0; r < kStrip; ++r) ac[r] = (i0 + r < la) ? base_at(a, i0 + r) : 4u;
-            int hl[kStrip];
+            int hl[kStrip], el[kStrip];
 #pragma unroll
-            for (int r = 0; r < kStrip; ++r) hl[r] = 0;   // H(i, 0) = 0
+            for (int r = 0; r < kStrip; ++r) { hl[r] = 0; el[r] = NEG; }   // H(i, 0) = 0, E(i, 0) = -inf
             int diag_top = 0;                                // H(i0, 0) = 0
             for (int j = 1; j <= lb; ++j) {
                 const uint32_t c = base_at(b, j - 1);
                 int up = (i0 == 0) ? 0 : bnd[(uint64_t)j * nthr];   // H(i0, j)
+                int fup = NEG;                                        // F(i0, j)
+                if (AFFINE && i0 != 0) fup = bndf[(uint64_t)j * nthr];
                 int diag = diag_top;                                  // H(i0, j-1)
                 diag_top = up;
 #pragma unroll
                 for (int r = 0; r < kStrip; ++r) {
                     const int s = (ac[r] == c) ? sc.match : sc.mismatch;
                     int h = max(0, diag + s);
-                    h = max(h, up - sc.gap);
-                    h = max(h, hl[r] - sc.gap);
+                    if (AFFINE) {
+                        const int e = max(el[r] - sc.gap, hl[r] - goe);
+                        const int f = max(fup - sc.gap, up - goe);
+                        h = max(h, max(e, f));
+                        el[r] = e;
+                        fup = f;
+                    } else {
+                        h = max(h, up - sc.gap);
+                        h = max(h, hl[r] - sc.gap);
+                    }
                     diag = hl[r];
                     hl[r] = h;
                     up = h;
                     if (i0 + r < la) best = max(best, h);
                 }
                 bnd[(uint64_t)j * nthr] = hl[kStrip - 1];
+                if (AFFINE) bndf[(uint64_t)j * nthr] = fup;
             }
         }
         job.out[o] = convert(best, la, lb, sc.conversion);
@@ -135,14 +156,17 @@ int run_general(const GeneralJob &job, const Scoring &sc, int sm_count, cudaStre
     // the boundary row needs (max column count + 1) ints per thread
     const uint32_t maxlb = job.B.stride * kBasesPerWord;
     uint64_t blocks = (uint64_t)std::max(sm_count, 1) * 8;
-    const uint64_t per_thread = (uint64_t)(maxlb + 1) * sizeof(int);
+    const uint64_t per_thread = (uint64_t)(maxlb + 1) * sizeof(int) * (sc.gap_open > 0 ? 2 : 1);
     const uint64_t budget = 1ull << 30;   // at most 1 GiB of boundary rows
     while (blocks > 1 && blocks * threads * per_thread > budget) blocks /= 2;
     const uint64_t need_blocks = (units + threads - 1) / threads;
     if (blocks > need_blocks) blocks = need_blocks;
     int *scratch = nullptr;
     GBD_CUDA_TRY(cudaMallocAsync((void **)&scratch, blocks * threads * per_thread, stream));
-    sw_general_kernel<<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units);
+    if (sc.gap_open > 0)
+        sw_general_kernel<true><<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units);
+    else
+        sw_general_kernel<false><<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units);
     note_launches(1);
     cudaError_t le = cudaGetLastError();
     cudaError_t fe = cudaFreeAsync(scratch, stream);
@@ -158,14 +182,17 @@ int run_general_in(const GeneralJob &job, const Scoring &sc, int *scratch, uint6
     const uint64_t units = (job.a1 - job.a0) * (job.b1 - job.b0);
     if (units == 0) return GBD_OK;
     const int threads = 128;
-    const uint64_t per_thread = (uint64_t)job.B.stride * kBasesPerWord + 1;   // ints
+    const uint64_t per_thread = ((uint64_t)job.B.stride * kBasesPerWord + 1) * (sc.gap_open > 0 ? 2 : 1);   // ints
     uint64_t blocks = (uint64_t)std::max(sm_count, 1) * 8;
     while (blocks > 0 && blocks * threads * per_thread > scratch_ints) --blocks;
     if (blocks == 0)
         return fail(GBD_EINVAL, "the boundary rows of one thread block do not fit the scratch area");
     const uint64_t need_blocks = (units + threads - 1) / threads;
     if (blocks > need_blocks) blocks = need_blocks;
-    sw_general_kernel<<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units);
+    if (sc.gap_open > 0)
+        sw_general_kernel<true><<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units);
+    else
+        sw_general_kernel<false><<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units);
     note_launches(1);
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) return cuda_fail(le, "sw_general_kernel launch");

@@ -33,6 +33,7 @@ EXPORTS = [
     "gbd_batch", "gbd_server_create", "gbd_server_submit", "gbd_server_poll",
     "gbd_server_wait", "gbd_server_destroy", "gbd_last_error", "gbd_probe_op_rate",
     "gbd_kernel_launches", "gbd_tile_noalloc", "gbd_sqdist_square", "gbd_gram_apply", "gbd_mds",
+    "gbd_tile_hits", "gbd_threshold_components", "gbd_tri_components",
 ]
 
 
@@ -40,7 +41,12 @@ class GbdParams(ctypes.Structure):
     _fields_ = [("match", ctypes.c_int16), ("mismatch", ctypes.c_int16),
                 ("gap", ctypes.c_int16), ("conversion", ctypes.c_int16),
                 ("kernel", ctypes.c_int32), ("hbm_budget", ctypes.c_uint64),
-                ("timeout_us", ctypes.c_uint32)]
+                ("timeout_us", ctypes.c_uint32), ("gap_open", ctypes.c_int16)]
+
+
+class GbdThreshold(ctypes.Structure):
+    """Hit rule d <= abs_max and d * den <= num * max(la, lb) (97 % homology: 3/100)."""
+    _fields_ = [("num", ctypes.c_uint32), ("den", ctypes.c_uint32), ("abs_max", ctypes.c_uint32)]
 
 
 class GbdError(RuntimeError):
@@ -76,6 +82,10 @@ def _declare(lib):
         "gbd_sqdist_square": ([vp, vp, u64, vp, u64, ctypes.POINTER(ctypes.c_int32), vp], ci),
         "gbd_gram_apply": ([vp, vp, u64, u64, ctypes.c_int32, vp, u32, vp, vp], ci),
         "gbd_mds": ([vp, vp, u64, vp, u32, u32, u32, vp, vp, vp], ci),
+        "gbd_tile_hits": ([vp, vp, u64, u64, vp, u64, u64, ctypes.POINTER(GbdThreshold), vp, u64, vp, u64,
+                           vp, vp, vp, vp], ci),
+        "gbd_threshold_components": ([vp, vp, ctypes.POINTER(GbdThreshold), vp, vp, vp, vp], ci),
+        "gbd_tri_components": ([vp, vp, vp, ctypes.POINTER(GbdThreshold), vp, vp, vp], ci),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -237,6 +247,32 @@ def gbd_mds(ctx: int, d_tri, n: int, d_omega, k: int, r: int, q: int, d_lambda, 
     """Classical MDS by randomized SVD: r eigenvalues and n x r coordinates (device)."""
     _check(_lib.gbd_mds(ctx, _ptr(d_tri), n, _ptr(d_omega), k, r, q, _ptr(d_lambda), _ptr(d_coords),
                         _stream(stream)))
+
+
+def threshold(num: int = 3, den: int = 100, abs_max: int = 65535) -> GbdThreshold:
+    return GbdThreshold(num, den, abs_max)
+
+
+def gbd_tile_hits(ctx: int, A: int, a0: int, a1: int, B: int, b0: int, b1: int, th: GbdThreshold,
+                  d_out=None, ld: int = 0, d_hits=None, hit_capacity: int = 0, d_hit_count=None,
+                  d_ref_labels=None, d_row_labels=None, stream=None) -> None:
+    """Rectangle with the threshold epilogue (hit list and/or row annotation)."""
+    _check(_lib.gbd_tile_hits(ctx, A, a0, a1, B, b0, b1, ctypes.byref(th), _ptr(d_out), ld, _ptr(d_hits),
+                              hit_capacity, _ptr(d_hit_count), _ptr(d_ref_labels), _ptr(d_row_labels),
+                              _stream(stream)))
+
+
+def gbd_threshold_components(ctx: int, s: int, th: GbdThreshold, d_labels, d_edges=None, d_tri=None,
+                             stream=None) -> None:
+    """Connected components of the threshold graph (labels = smallest read of each component)."""
+    _check(_lib.gbd_threshold_components(ctx, s, ctypes.byref(th), _ptr(d_labels), _ptr(d_edges), _ptr(d_tri),
+                                         _stream(stream)))
+
+
+def gbd_tri_components(ctx: int, s: int, d_tri, th: GbdThreshold, d_labels, d_edges=None, stream=None) -> None:
+    """Threshold-graph components from an already computed triangle of the set."""
+    _check(_lib.gbd_tri_components(ctx, s, _ptr(d_tri), ctypes.byref(th), _ptr(d_labels), _ptr(d_edges),
+                                   _stream(stream)))
 
 
 def gbd_kernel_launches() -> int:

@@ -179,8 +179,9 @@ def _codes_to_readset(codes: list[np.ndarray]) -> ReadSet:
 
 
 def reads_from_ancestors(st: Stream, ancestors: np.ndarray, n: int, len_lo: int, len_hi: int,
-                         p_sub: float, p_indel: float, chunk: int = 8192) -> ReadSet:
-    """n reads, each a mutated copy of a uniformly chosen ancestor, lengths U[len_lo, len_hi]."""
+                         p_sub: float, p_indel: float, chunk: int = 8192, return_parents: bool = False):
+    """n reads, each a mutated copy of a uniformly chosen ancestor, lengths U[len_lo, len_hi].
+    With return_parents, also the ancestor index of every read (a species label)."""
     parent_of = st.integers(0, len(ancestors) - 1, (n,))
     target = st.integers(len_lo, len_hi, (n,))
     codes: list[np.ndarray] = []
@@ -188,7 +189,8 @@ def reads_from_ancestors(st: Stream, ancestors: np.ndarray, n: int, len_lo: int,
         sub = Stream(int(st.key), 1000 + c0 // chunk)
         codes += mutate(sub, ancestors, parent_of[c0:c0 + chunk], target[c0:c0 + chunk],
                         p_sub, p_indel)
-    return _codes_to_readset(codes)
+    rs = _codes_to_readset(codes)
+    return (rs, parent_of.astype(np.int32)) if return_parents else rs
 
 
 def ancestor_tree(st: Stream, length: int, branching=(4, 5, 10), div_lo=0.02, div_hi=0.08,

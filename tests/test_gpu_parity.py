@@ -149,6 +149,31 @@ def test_other_scores_raw_score_mode(gbd, scores):
     np.testing.assert_array_equal(got.astype(np.int64), want)
 
 
+@pytest.mark.parametrize("scores", [(1, -1, 1, 2), (2, -3, 1, 3), (1, -2, 2, 1)])
+def test_affine_gaps_exact(gbd, scores):
+    """Affine gaps (gap_open > 0) on the general kernel against the oracle's Gotoh mode:
+    distances of the 150-read workload, and raw scores of edge-length reads."""
+    import torch
+    m, x, g, go = scores
+    rs = synth.workload_plain_small()
+    ctx = _ctx(gbd, "auto", match=m, mismatch=x, gap=g, gap_open=go)
+    got = _all_pairs(gbd, ctx, rs)
+    np.testing.assert_array_equal(got, oracle.all_pairs(rs, match=m, mismatch=x, gap=g, gap_open=go))
+    edge = synth.from_strings(_edge_reads()[:30])
+    ctx2 = _ctx(gbd, "auto", match=m, mismatch=x, gap=g, gap_open=go, conversion=gbd.GBD_CONV_SCORE)
+    got2 = _all_pairs(gbd, ctx2, edge)
+    pi, pj = np.triu_indices(edge.n, 1)
+    want2 = oracle.pair_scores(edge, pi, pj, match=m, mismatch=x, gap=g, gap_open=go)
+    np.testing.assert_array_equal(got2.astype(np.int64), want2)
+
+
+def test_affine_gap_rejected_by_systolic_and_negative(gbd):
+    with pytest.raises(gbd.GbdError):
+        _ctx(gbd, "systolic", gap_open=2)
+    with pytest.raises(gbd.GbdError):
+        _ctx(gbd, "auto", gap_open=-1)
+
+
 def test_batch_matches_per_sample(gbd):
     import torch
     samples = synth.workload_batched(n_samples=5, n_lo=20, n_hi=120)
