@@ -505,7 +505,8 @@ def run_batch_mode(args):
 
     res = {}
     for name, fn in (("plain_per_sample", plain), ("batched", batched)):
-        fn()                                   # warm-up (also builds the schedules)
+        for _ in range(4):                     # warm-up: schedules, and the batch autotuner's
+            fn()                               # three timed candidates plus its pick
         torch.cuda.synchronize()
         ts = []
         for _ in range(args.steps):
@@ -516,7 +517,8 @@ def run_batch_mode(args):
         t = float(np.median(ts))
         res[name] = {"seconds": t, "pairs_per_s": pairs / t, "gcups": cells / t / 1e9}
     same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_p))
-    line = {"mode": "batch", "workload": f"{len(samples)} samples, read counts "
+    tuning = gbd.gbd_batch_tuning(ctx.handle)
+    line = {"mode": "batch", "autotuner": tuning, "workload": f"{len(samples)} samples, read counts "
             f"{min(s.n for s in samples)}-{max(s.n for s in samples)}, lengths U[150,500]",
             "pairs": pairs, "cells": cells, "identical_outputs": bool(same), **res,
             "speedup": res["plain_per_sample"]["seconds"] / res["batched"]["seconds"]}

@@ -112,6 +112,14 @@ int gbd_tile(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd
 int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns,
               uint16_t *const *d_tris, void *stream);
 
+/* The batched launch tunes itself online: the first calls with a new list of samples and
+ * outputs run the launch group with work units of 1, 0.5 and 2 times the cost model's size
+ * (timed with events on `stream`; each of these calls first waits for the previous one to
+ * finish), and from the fourth call on the fastest is replayed as a CUDA graph.  Results are
+ * identical for every candidate.  gbd_batch_tuning reports the three timings (ms, 0 until
+ * measured), the scale in use and whether tuning has finished; ENOTFOUND before any batch. */
+int gbd_batch_tuning(const gbd_ctx *ctx, double *trial_ms, double *scale, int *done);
+
 /* Serving (a5): a resident reference set answers query batches with distance rows.
  * submit copies the queries (host pointers, nq reads) and returns at once with a
  * ticket; the request is admitted when its memory fits the budget beside the requests

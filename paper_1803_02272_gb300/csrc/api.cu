@@ -213,6 +213,12 @@ static int check_threshold(const gbd_threshold *th)
 
 
 // Last captured batch: its inputs, persistent job table and plan, and the graph.
+// Online autotuner of the batched launch: the first calls with a new set of samples
+// replay the launch group built with each candidate work-unit size (the cost model's
+// piece times kPieceScales[t]), timed with events; the next call keeps the fastest.
+constexpr int kTrials = 3;
+constexpr double kPieceScales[kTrials] = {1.0, 0.5, 2.0};
+
 struct BatchGraph {
     std::vector<uint64_t> ids;
     std::vector<uint16_t *> outs;
@@ -222,6 +228,16 @@ struct BatchGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t kernels = 0;
+    // inputs of the plan, kept to rebuild it with another piece scale
+    std::vector<SysEntry> entries;
+    std::vector<uint8_t> rows;
+    double mean_len = 0.0;
+    // autotuner state
+    int trial = 0;                    // candidate being timed; kTrials = tuning finished
+    bool timing = false;              // events t0/t1 bracket the last launch
+    double trial_ms[kTrials] = {0, 0, 0};
+    double scale = 1.0;               // piece scale of the current graph
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
     bool matches(const gbd_set *const *samples, uint64_t ns, uint16_t *const *d_tris, int conv) const
     {
         if (ids.size() != ns || conversion != conv) return false;
@@ -239,12 +255,17 @@ void free_batch_cache(gbd_ctx *ctx)
     if (bg->graph) cudaGraphDestroy(bg->graph);
     if (bg->d_jobs) cudaFree(bg->d_jobs);
     free_plan(bg->plan, nullptr);
+    if (bg->t0) cudaEventDestroy(bg->t0);
+    if (bg->t1) cudaEventDestroy(bg->t1);
     delete bg;
     ctx->batch_cache = nullptr;
 }
 
 // Builds the batch's job table and plan (persistent) and records its launch group on the
 // context's capture stream.
+static int record_batch_graph(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const *samples, uint64_t ns,
+                              uint16_t *const *d_tris, double scale);
+
 static int capture_batch(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const *samples, uint64_t ns,
                          uint16_t *const *d_tris)
 {
@@ -289,8 +310,25 @@ static int capture_batch(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const *sam
         GBD_CUDA_TRY(cudaMalloc((void **)&bg->d_jobs, ns * sizeof(SysJob)));
         GBD_CUDA_TRY(cudaMemcpy(bg->d_jobs, jobs.data(), ns * sizeof(SysJob), cudaMemcpyHostToDevice));
     }
-    const double mean_len = n_sum > 0 ? len_sum / n_sum : 0.0;
-    int rc = build_plan(entries, rows, bg->plan, true, cap, 0, mean_len, ctx->sm_count);
+    bg->mean_len = n_sum > 0 ? len_sum / n_sum : 0.0;
+    bg->entries.swap(entries);
+    bg->rows.swap(rows);
+    GBD_CUDA_TRY(cudaEventCreate(&bg->t0));
+    GBD_CUDA_TRY(cudaEventCreate(&bg->t1));
+    return record_batch_graph(ctx, bg, samples, ns, d_tris, kPieceScales[0]);
+}
+
+// (Re)builds the plan with the given piece scale and records the launch group as a graph.
+// The previous graph, if any, must have finished.
+static int record_batch_graph(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const *samples, uint64_t ns,
+                              uint16_t *const *d_tris, double scale)
+{
+    cudaStream_t cap = ctx->capture;
+    if (bg->exec) { cudaGraphExecDestroy(bg->exec); bg->exec = nullptr; }
+    if (bg->graph) { cudaGraphDestroy(bg->graph); bg->graph = nullptr; }
+    free_plan(bg->plan, nullptr);
+    bg->scale = scale;
+    int rc = build_plan(bg->entries, bg->rows, bg->plan, true, cap, 0, bg->mean_len, ctx->sm_count, scale);
     if (rc != GBD_OK) return rc;
     const uint64_t launches0 = gbd_kernel_launches();
     GBD_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
@@ -648,9 +686,55 @@ int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns, uint16_t
             return rc;
         }
         fresh = true;                        // the capture already counted its kernels
+    } else if (bg->trial < kTrials) {
+        // autotuning: read the time of the previous candidate's launch, move to the next
+        // candidate (or, after the last, to the fastest) and record its graph
+        if (bg->timing) {
+            GBD_CUDA_TRY(cudaEventSynchronize(bg->t1));
+            float ms = 0.f;
+            GBD_CUDA_TRY(cudaEventElapsedTime(&ms, bg->t0, bg->t1));
+            bg->trial_ms[bg->trial] = ms;
+            bg->timing = false;
+            ++bg->trial;
+        }
+        double next = kPieceScales[0];
+        if (bg->trial < kTrials) {
+            next = kPieceScales[bg->trial];
+        } else {
+            int best = 0;
+            for (int t = 1; t < kTrials; ++t)
+                if (bg->trial_ms[t] < bg->trial_ms[best]) best = t;
+            next = kPieceScales[best];
+        }
+        if (next != bg->scale || bg->trial < kTrials) {
+            rc = record_batch_graph(ctx, bg, samples, ns, d_tris, next);
+            if (rc != GBD_OK) {
+                free_batch_cache(ctx);
+                return rc;
+            }
+            fresh = true;
+        }
     }
+    const bool time_it = bg->trial < kTrials;
+    if (time_it) GBD_CUDA_TRY(cudaEventRecord(bg->t0, st));
     GBD_CUDA_TRY(cudaGraphLaunch(bg->exec, st));
+    if (time_it) {
+        GBD_CUDA_TRY(cudaEventRecord(bg->t1, st));
+        bg->timing = true;
+    }
     if (!fresh) note_launches(bg->kernels);
+    return GBD_OK;
+}
+
+int gbd_batch_tuning(const gbd_ctx *ctx, double *trial_ms, double *scale, int *done)
+{
+    if (!ctx) return fail(GBD_EINVAL, "gbd_batch_tuning: NULL context");
+    const BatchGraph *bg = static_cast<const BatchGraph *>(ctx->batch_cache);
+    if (!bg) return fail(GBD_ENOTFOUND, "gbd_batch_tuning: no batch has run on this context");
+    for (int t = 0; t < kTrials; ++t)
+        if (trial_ms) trial_ms[t] = bg->trial_ms[t];
+    if (scale) *scale = bg->scale;
+    if (done) *done = bg->trial >= kTrials ? 1 : 0;
     return GBD_OK;
 }
 

@@ -11,9 +11,11 @@
 //                         Y = -2^(s-1) (P - 1 mean^T); J W J X = J W (J X) needs no
 //                         centred copy of W
 //   orthonormalise        Gram S = Y^T Y (float64), Cholesky S = R^T R, Q = Y R^-1
-//                         (columns whose pivot falls below a floor dropped), twice
-//   eigenpairs of B       B = Q^T (G Q) by the same Gram kernel, Jacobi, eigenvalues
-//                         sorted down, coordinates Q V_r diag(max(lambda, 0)^1/2)
+//                         (columns whose pivot falls below a floor dropped); once between
+//                         products, twice for the basis that B is formed on
+//   eigenpairs of B       B = Q^T (G Q) by the same Gram kernel, Jacobi (float32 with
+//                         float64 angles), eigenvalues sorted down, coordinates
+//                         Q V_r diag(max(lambda, 0)^1/2)
 // All reductions run in a fixed order, so results do not depend on scheduling.
 #include <cuda_fp16.h>
 
@@ -52,6 +54,7 @@ __global__ void tri_max_kernel(const uint16_t *__restrict__ tri, uint64_t m, uin
 
 // ------------------------------------------------------------------ triangle -> fp16 square
 constexpr int ST = 64;   // square tile
+constexpr uint64_t SUPER = 16;   // tiles per super-tile side
 
 __device__ __forceinline__ uint64_t tri_index(uint64_t i, uint64_t j, uint64_t n)
 {
@@ -64,6 +67,18 @@ __device__ __forceinline__ uint16_t sq_half(uint32_t d, float scale)
     return __half_as_ushort(__float2half_rn(f * f * scale));
 }
 
+// Two packed distances (low and high 16 bits) to two packed fp16 values of d^2 * scale.
+// float(d) for d < 2^16 comes from the float bit pattern 2^23 + d minus 2^23 (exact),
+// which keeps the conversion off the slow integer-to-float path, and the pair is rounded
+// to fp16 by one paired conversion.
+__device__ __forceinline__ uint32_t sq_half2(uint32_t pair, float scale)
+{
+    const float lo = __uint_as_float(0x4B000000u | (pair & 0xffffu)) - 8388608.0f;
+    const float hi = __uint_as_float(0x4B000000u | (pair >> 16)) - 8388608.0f;
+    const __half2 h = __floats2half2_rn(lo * lo * scale, hi * hi * scale);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
 // Tile (I, J), I <= J, of the square: W[I-block][J-block] from the triangle, and its
 // transpose W[J-block][I-block] through shared memory.  Off-diagonal tiles whose columns
 // all lie below n (all but a thin margin) take the fast path: each warp handles whole
@@ -71,21 +86,27 @@ __device__ __forceinline__ uint16_t sq_half(uint32_t d, float scale)
 // with a shuffle), 128-byte stores; the rest go element by element.
 __global__ void __launch_bounds__(256)
 sqdist_square_kernel(const uint16_t *__restrict__ tri, uint64_t n, uint64_t ld, float scale,
-                     uint16_t *__restrict__ W, uint64_t ntiles, int aligned)
+                     uint16_t *__restrict__ W, uint64_t nsuper, int aligned)
 {
     __shared__ uint16_t t[ST][ST + 2];
     const uint64_t T = ld / ST;
-    const uint64_t lin = blockIdx.x;
-    if (lin >= ntiles) return;
-    // row I of the tile triangle holds T - I tiles (float estimate, then exact fix-up)
-    const float b = 2.0f * (float)T + 1.0f;
-    int64_t I = (int64_t)((b - sqrtf(fmaxf(b * b - 8.0f * (float)lin, 0.0f))) * 0.5f);
-    auto row_start = [&](int64_t r) { return (uint64_t)r * T - (uint64_t)r * (uint64_t)(r - 1) / 2; };
-    if (I < 0) I = 0;
-    while (I > 0 && row_start(I) > lin) --I;
-    while ((uint64_t)(I + 1) < T && row_start(I + 1) <= lin) ++I;
-    const uint64_t J = (uint64_t)I + (lin - row_start(I));
-    const uint64_t i0 = (uint64_t)I * ST, j0 = J * ST;
+    // Blocks walk super-tiles of SUPER x SUPER tiles (upper triangle of super-tiles, row by
+    // row), and the tiles of a super-tile row by row, so the blocks resident at one time
+    // write a compact region of the square in both of its orientations.
+    const uint64_t sup = blockIdx.x / (SUPER * SUPER), within = blockIdx.x % (SUPER * SUPER);
+    const uint64_t TS = (T + SUPER - 1) / SUPER;
+    if (sup >= nsuper) return;
+    // row SI of the super-tile triangle holds TS - SI super-tiles (float estimate, exact fix-up)
+    const float b = 2.0f * (float)TS + 1.0f;
+    int64_t SI = (int64_t)((b - sqrtf(fmaxf(b * b - 8.0f * (float)sup, 0.0f))) * 0.5f);
+    auto row_start = [&](int64_t r) { return (uint64_t)r * TS - (uint64_t)r * (uint64_t)(r - 1) / 2; };
+    if (SI < 0) SI = 0;
+    while (SI > 0 && row_start(SI) > sup) --SI;
+    while ((uint64_t)(SI + 1) < TS && row_start(SI + 1) <= sup) ++SI;
+    const uint64_t SJ = (uint64_t)SI + (sup - row_start(SI));
+    const uint64_t I = (uint64_t)SI * SUPER + within / SUPER, J = SJ * SUPER + within % SUPER;
+    if (I > J || J >= T) return;
+    const uint64_t i0 = I * ST, j0 = J * ST;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const bool fast = aligned && (uint64_t)I != J && j0 + ST <= n;
@@ -109,8 +130,7 @@ sqdist_square_kernel(const uint16_t *__restrict__ tri, uint64_t n, uint64_t ld, 
             uint32_t hi = __shfl_down_sync(0xffffffffu, lo[q], 1);     // the next lane's word
             if (lane == 31) hi = ex[q];
             const uint32_t pair = odd[q] ? __funnelshift_r(lo[q], hi, 16) : lo[q];
-            const uint32_t pk =
-                (uint32_t)sq_half(pair & 0xffffu, scale) | ((uint32_t)sq_half(pair >> 16, scale) << 16);
+            const uint32_t pk = sq_half2(pair, scale);
             t[r][2 * lane] = (uint16_t)(pk & 0xffffu);
             t[r][2 * lane + 1] = (uint16_t)(pk >> 16);
             *reinterpret_cast<uint32_t *>(W + (i0 + r) * ld + j0 + 2 * lane) = pk;
@@ -357,81 +377,72 @@ chol_inverse_kernel(const double *__restrict__ S_in, uint32_t k, double floor_re
 }
 
 // ------------------------------------------------------------------ symmetric eigensolver
-// Cyclic Jacobi with the round-robin ordering (k/2 disjoint rotations per round, k-1
-// rounds per sweep), float64, one block.  mode 0 (orthonormalisation of Y, S = Y^T Y):
-// T = V diag(w), w = s^-1/2 where s > floor * max s, else 0.  mode 1 (eigenpairs of B):
-// the r largest eigenvalues in order into lambda, T = V_r diag(max(lambda, 0)^1/2).
-// flags bit 0: Jacobi did not converge; bit 1: non-finite input.
+// Eigenpairs of the small symmetric B = Q^T G Q: cyclic Jacobi with the round-robin
+// ordering (k/2 disjoint rotations per round, k-1 rounds per sweep), one block.  The
+// matrix and the rotations live in float32 (this part's output is float32, and float64
+// arithmetic is scarce on this GPU); each rotation angle is computed in float64.  A pair is
+// rotated only while its off-diagonal entry exceeds 1e-6 of the matrix norm (threshold
+// Jacobi); the sweeps stop when one makes no rotation.  Outputs: the r largest eigenvalues in order into lambda, and
+// T = V_r diag(max(lambda, 0)^1/2).  flags bit 0: no convergence; bit 1: non-finite input.
 constexpr int kMaxJacobiK = 112;
 constexpr int kMaxSweeps = 40;
+constexpr double kJacobiTol = 1e-6;   // about 17 float32 ulps
 
 __global__ void __launch_bounds__(256)
-jacobi_kernel(const double *__restrict__ S_in, uint32_t k, int mode, uint32_t r, double floor_rel,
-              float *__restrict__ T, float *__restrict__ lambda, uint32_t *flags)
+jacobi_kernel(const double *__restrict__ S_in, uint32_t k, uint32_t r, float *__restrict__ T,
+              float *__restrict__ lambda, uint32_t *flags)
 {
-    extern __shared__ double sd[];
-    double *A = sd;                   // k x k
-    double *V = sd + k * k;           // k x k
-    __shared__ double cs[kMaxJacobiK / 2], sn[kMaxJacobiK / 2];
+    extern __shared__ float sf[];
+    float *A = sf;                    // k x k
+    float *V = sf + k * k;            // k x k
+    __shared__ float cs[kMaxJacobiK / 2], sn[kMaxJacobiK / 2];
     __shared__ int pp[kMaxJacobiK / 2], qq[kMaxJacobiK / 2];
     __shared__ double red[256];
-    __shared__ int done;
+    __shared__ int rotated;
+    __shared__ double fro;
     __shared__ int order[kMaxJacobiK];
     const uint32_t kk = k * k;
+    double tot = 0.0;
     for (uint32_t e = threadIdx.x; e < kk; e += blockDim.x) {
         const uint32_t i = e / k, j = e % k;
         const double a = 0.5 * (S_in[i * k + j] + S_in[j * k + i]);
-        A[e] = a;
-        V[e] = (i == j) ? 1.0 : 0.0;
+        A[e] = (float)a;
+        V[e] = (i == j) ? 1.f : 0.f;
+        tot += a * a;
         if (!isfinite(a)) atomicOr(flags, 2u);
     }
+    red[threadIdx.x] = tot;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) fro = sqrt(red[0]);
     __syncthreads();
     const uint32_t half = k / 2;
-    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-        // convergence test: off-diagonal mass against the total
-        double off = 0.0, tot = 0.0;
-        for (uint32_t e = threadIdx.x; e < kk; e += blockDim.x) {
-            const double a = A[e];
-            tot += a * a;
-            if (e / k != e % k) off += a * a;
-        }
-        red[threadIdx.x] = off;
+    bool converged = false;
+    for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
+        if (threadIdx.x == 0) rotated = 0;
         __syncthreads();
-        for (int s = 128; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        const double off_sum = red[0];
-        __syncthreads();
-        red[threadIdx.x] = tot;
-        __syncthreads();
-        for (int s = 128; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) done = (off_sum <= 1e-30 * red[0]) || off_sum == 0.0;
-        __syncthreads();
-        if (done) break;
-        if (sweep == kMaxSweeps - 1) {
-            if (threadIdx.x == 0) atomicOr(flags, 1u);
-            break;
-        }
         for (uint32_t round = 0; round + 1 < k; ++round) {
             if (threadIdx.x < half) {
                 // circle method: position 0 fixed, positions 1..k-1 rotate
                 auto at = [&](uint32_t pos) -> uint32_t { return pos == 0 ? 0u : 1u + (pos - 1 + round) % (k - 1); };
                 uint32_t p = at(threadIdx.x), q = at(k - 1 - threadIdx.x);
                 if (p > q) { const uint32_t t = p; p = q; q = t; }
-                const double apq = A[p * k + q];
+                const double apq = A[p * k + q], app = A[p * k + p], aqq = A[q * k + q];
                 double c = 1.0, s = 0.0;
-                if (apq != 0.0) {
-                    const double theta = (A[q * k + q] - A[p * k + p]) / (2.0 * apq);
+                // negligible against the matrix norm (float32 cannot resolve less)
+                const double floor = kJacobiTol * fro;
+                if (fabs(apq) > floor) {
+                    const double theta = (aqq - app) / (2.0 * apq);
                     const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
                     c = 1.0 / sqrt(t * t + 1.0);
                     s = t * c;
+                    rotated = 1;
                 }
-                cs[threadIdx.x] = c;
-                sn[threadIdx.x] = s;
+                cs[threadIdx.x] = (float)c;
+                sn[threadIdx.x] = (float)s;
                 pp[threadIdx.x] = (int)p;
                 qq[threadIdx.x] = (int)q;
             }
@@ -439,12 +450,14 @@ jacobi_kernel(const double *__restrict__ S_in, uint32_t k, int mode, uint32_t r,
             // columns: A <- A P, V <- V P
             for (uint32_t e = threadIdx.x; e < half * k; e += blockDim.x) {
                 const uint32_t pr = e / k, row = e % k;
+                const float s = sn[pr];
+                if (s == 0.f) continue;
                 const int p = pp[pr], q = qq[pr];
-                const double c = cs[pr], s = sn[pr];
-                const double ap = A[row * k + p], aq = A[row * k + q];
+                const float c = cs[pr];
+                const float ap = A[row * k + p], aq = A[row * k + q];
                 A[row * k + p] = c * ap - s * aq;
                 A[row * k + q] = s * ap + c * aq;
-                const double vp = V[row * k + p], vq = V[row * k + q];
+                const float vp = V[row * k + p], vq = V[row * k + q];
                 V[row * k + p] = c * vp - s * vq;
                 V[row * k + q] = s * vp + c * vq;
             }
@@ -452,44 +465,38 @@ jacobi_kernel(const double *__restrict__ S_in, uint32_t k, int mode, uint32_t r,
             // rows: A <- P^T A
             for (uint32_t e = threadIdx.x; e < half * k; e += blockDim.x) {
                 const uint32_t pr = e / k, col = e % k;
+                const float s = sn[pr];
+                if (s == 0.f) continue;
                 const int p = pp[pr], q = qq[pr];
-                const double c = cs[pr], s = sn[pr];
-                const double ap = A[p * k + col], aq = A[q * k + col];
+                const float c = cs[pr];
+                const float ap = A[p * k + col], aq = A[q * k + col];
                 A[p * k + col] = c * ap - s * aq;
                 A[q * k + col] = s * ap + c * aq;
             }
             __syncthreads();
         }
+        converged = (rotated == 0);
+        __syncthreads();
     }
-    __syncthreads();
+    if (!converged && threadIdx.x == 0) atomicOr(flags, 1u);
     // eigenvalues on the diagonal; rank them largest first (ties by index)
     for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
-        const double li = A[i * k + i];
+        const float li = A[i * k + i];
         int rank = 0;
         for (uint32_t j = 0; j < k; ++j) {
-            const double lj = A[j * k + j];
+            const float lj = A[j * k + j];
             if (lj > li || (lj == li && j < i)) ++rank;
         }
         order[rank] = (int)i;
     }
     __syncthreads();
-    if (mode == 0) {
-        const double smax = A[order[0] * k + order[0]];
-        for (uint32_t e = threadIdx.x; e < kk; e += blockDim.x) {
-            const uint32_t row = e / k, col = e % k;
-            const double s = A[col * k + col];
-            const double w = (s > floor_rel * smax && s > 0.0) ? 1.0 / sqrt(s) : 0.0;
-            T[e] = (float)(V[row * k + col] * w);
-        }
-    } else {
-        for (uint32_t e = threadIdx.x; e < k * r; e += blockDim.x) {
-            const uint32_t row = e / r, a = e % r;
-            const int col = order[a];
-            const double lam = A[col * k + col];
-            T[e] = (float)(V[row * k + col] * sqrt(fmax(lam, 0.0)));
-        }
-        for (uint32_t a = threadIdx.x; a < r; a += blockDim.x) lambda[a] = (float)A[order[a] * k + order[a]];
+    for (uint32_t e = threadIdx.x; e < k * r; e += blockDim.x) {
+        const uint32_t row = e / r, a = e % r;
+        const int col = order[a];
+        const float lam = A[col * k + col];
+        T[e] = V[row * k + col] * sqrtf(fmaxf(lam, 0.f));
     }
+    for (uint32_t a = threadIdx.x; a < r; a += blockDim.x) lambda[a] = A[order[a] * k + order[a]];
 }
 
 // ------------------------------------------------------------------ Out = A T
@@ -626,6 +633,7 @@ int xty(const float *A, const float *B, MdsWork &w)
 }
 
 size_t jacobi_smem(uint32_t k) { return 2 * (size_t)k * k * sizeof(double); }
+size_t jacobi_smem_f32(uint32_t k) { return 2 * (size_t)k * k * sizeof(float); }
 
 int apply(const float *A, const float *T, uint32_t m, float *Out, MdsWork &w)
 {
@@ -635,13 +643,15 @@ int apply(const float *A, const float *T, uint32_t m, float *Out, MdsWork &w)
     return GBD_OK;
 }
 
-// Q = orthonormal basis of the range of Y (Cholesky QR, twice).  Y is overwritten.
+// Q = basis of the range of Y by Cholesky QR, `passes` times (two give an orthonormal
+// basis to working precision; one suffices between the products of the subspace
+// iteration, which only need the right span).  Y is overwritten.
 constexpr double kOrthFloor = 1e-12;
 
-int orthonormalise(float *Y, float *Q, MdsWork &w)
+int orthonormalise(float *Y, float *Q, MdsWork &w, int passes)
 {
     float *src = Y, *dst = Q;
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < passes; ++pass) {
         int rc = xty(src, src, w);
         if (rc != GBD_OK) return rc;
         chol_inverse_kernel<<<1, 256, jacobi_smem(w.k), w.st>>>(w.gram, w.k, kOrthFloor, w.T, w.flags + 1);
@@ -650,9 +660,11 @@ int orthonormalise(float *Y, float *Q, MdsWork &w)
         if (rc != GBD_OK) return rc;
         std::swap(src, dst);
     }
-    // two passes: the result is back in Y; copy to Q
-    cudaError_t e = cudaMemcpyAsync(Q, Y, w.n * w.k * sizeof(float), cudaMemcpyDeviceToDevice, w.st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    // after an even number of passes the result is back in Y
+    if (src != Q) {
+        cudaError_t e = cudaMemcpyAsync(Q, src, w.n * w.k * sizeof(float), cudaMemcpyDeviceToDevice, w.st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    }
     return GBD_OK;
 }
 
@@ -663,7 +675,7 @@ int configure_kernels()
     std::lock_guard<std::mutex> lk(mu);
     if (done) return GBD_OK;
     GBD_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)jacobi_smem(kMaxJacobiK)));
+                                      (int)jacobi_smem_f32(kMaxJacobiK)));
     GBD_CUDA_TRY(cudaFuncSetAttribute(xty_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(2 * kGramRows * kMaxJacobiK * sizeof(double))));
     GBD_CUDA_TRY(cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -705,11 +717,13 @@ int sqdist_square_impl(gbd_ctx *ctx, const uint16_t *d_tri, uint64_t n, uint16_t
     while (d2 * std::ldexp(1.0, -s) > 65504.0) ++s;
     *shift = s;
     const uint64_t T = ld / ST;
-    const uint64_t ntiles = T * (T + 1) / 2;
-    if (ntiles > 0x7fffffffull) return fail(GBD_EINVAL, "square too large");
+    const uint64_t TS = (T + SUPER - 1) / SUPER;
+    const uint64_t nsuper = TS * (TS + 1) / 2;
+    const uint64_t nblocks = nsuper * SUPER * SUPER;
+    if (nblocks > 0x7fffffffull) return fail(GBD_EINVAL, "square too large");
     const int aligned = (reinterpret_cast<uintptr_t>(d_tri) % 4) == 0 ? 1 : 0;
-    sqdist_square_kernel<<<(unsigned)ntiles, 256, 0, st>>>(d_tri, n, ld, (float)std::ldexp(1.0, -s), d_w, ntiles,
-                                                            aligned);
+    sqdist_square_kernel<<<(unsigned)nblocks, 256, 0, st>>>(d_tri, n, ld, (float)std::ldexp(1.0, -s), d_w, nsuper,
+                                                             aligned);
     GBD_LAUNCH_CHECK("sqdist_square_kernel");
     return GBD_OK;
 }
@@ -782,16 +796,16 @@ extern "C" int gbd_mds(gbd_ctx *ctx, const uint16_t *d_tri, uint64_t n, const fl
     if (rc == GBD_OK) rc = sqdist_square_impl(ctx, d_tri, n, W, ld, &shift, st);
     // range finder: Q = orth(G Omega), then q rounds of two products (G is symmetric)
     if (rc == GBD_OK) rc = gram_apply_in(W, shift, d_omega, Y, w, ctx->sm_count);
-    if (rc == GBD_OK) rc = orthonormalise(Y, Q, w);
+    if (rc == GBD_OK) rc = orthonormalise(Y, Q, w, q == 0 ? 2 : 1);
     for (uint32_t t = 0; rc == GBD_OK && t < 2 * q; ++t) {
         rc = gram_apply_in(W, shift, Q, Y, w, ctx->sm_count);
-        if (rc == GBD_OK) rc = orthonormalise(Y, Q, w);
+        if (rc == GBD_OK) rc = orthonormalise(Y, Q, w, t + 1 == 2 * q ? 2 : 1);
     }
     // B = Q^T G Q, eigenpairs, coordinates Q V_r diag(sqrt(max(lambda, 0)))
     if (rc == GBD_OK) rc = gram_apply_in(W, shift, Q, Y, w, ctx->sm_count);
     if (rc == GBD_OK) rc = xty(Q, Y, w);
     if (rc == GBD_OK) {
-        jacobi_kernel<<<1, 256, jacobi_smem(k), st>>>(w.gram, k, 1, r, 0.0, w.T, d_lambda, w.flags + 1);
+        jacobi_kernel<<<1, 256, jacobi_smem_f32(k), st>>>(w.gram, k, r, w.T, d_lambda, w.flags + 1);
         note_launches(1);
         cudaError_t le = cudaGetLastError();
         if (le != cudaSuccess) rc = cuda_fail(le, "jacobi_kernel launch");

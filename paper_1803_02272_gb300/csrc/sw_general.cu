@@ -16,7 +16,10 @@
 namespace gbd {
 namespace {
 
-constexpr int kStrip = 8;
+// Query rows per strip, held in registers.  Each strip passes its last row to the next
+// through the boundary rows in scratch (4 bytes read and written per column, twice with
+// affine gaps), so a taller strip cuts that traffic per cell.
+constexpr int kStrip = 16;
 
 __device__ __forceinline__ uint32_t base_at(const uint32_t *w, uint32_t k)
 {
@@ -138,6 +141,21 @@ sw_general_kernel(GeneralJob job, Scoring sc, int *__restrict__ scratch, uint64_
     }
 }
 
+// Blocks of 128 threads resident per SM for the kernel variant (one full wave is launched,
+// so the grid-stride loop spreads the pairs evenly).
+int resident_blocks(bool affine)
+{
+    static int cached[2] = {0, 0};
+    int &c = cached[affine ? 1 : 0];
+    if (c == 0) {
+        int b = 0;
+        cudaError_t e = affine ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sw_general_kernel<true>, 128, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sw_general_kernel<false>, 128, 0);
+        c = (e == cudaSuccess && b > 0) ? b : 4;
+    }
+    return c;
+}
+
 }  // namespace
 
 int run_general(const GeneralJob &job, const Scoring &sc, int sm_count, cudaStream_t stream)
@@ -155,7 +173,7 @@ int run_general(const GeneralJob &job, const Scoring &sc, int sm_count, cudaStre
     const int threads = 128;
     // the boundary row needs (max column count + 1) ints per thread
     const uint32_t maxlb = job.B.stride * kBasesPerWord;
-    uint64_t blocks = (uint64_t)std::max(sm_count, 1) * 8;
+    uint64_t blocks = (uint64_t)std::max(sm_count, 1) * resident_blocks(sc.gap_open > 0);
     const uint64_t per_thread = (uint64_t)(maxlb + 1) * sizeof(int) * (sc.gap_open > 0 ? 2 : 1);
     const uint64_t budget = 1ull << 30;   // at most 1 GiB of boundary rows
     while (blocks > 1 && blocks * threads * per_thread > budget) blocks /= 2;
@@ -183,7 +201,7 @@ int run_general_in(const GeneralJob &job, const Scoring &sc, int *scratch, uint6
     if (units == 0) return GBD_OK;
     const int threads = 128;
     const uint64_t per_thread = ((uint64_t)job.B.stride * kBasesPerWord + 1) * (sc.gap_open > 0 ? 2 : 1);   // ints
-    uint64_t blocks = (uint64_t)std::max(sm_count, 1) * 8;
+    uint64_t blocks = (uint64_t)std::max(sm_count, 1) * resident_blocks(sc.gap_open > 0);
     while (blocks > 0 && blocks * threads * per_thread > scratch_ints) --blocks;
     if (blocks == 0)
         return fail(GBD_EINVAL, "the boundary rows of one thread block do not fit the scratch area");

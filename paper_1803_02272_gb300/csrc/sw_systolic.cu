@@ -529,7 +529,7 @@ uint32_t tuned_piece(uint64_t pairs, double mean_len, int warps)
 
 int build_plan(const std::vector<SysEntry> &entries, const std::vector<uint8_t> &rows,
                SysPlan &plan, bool persistent, cudaStream_t stream, uint32_t piece_len,
-               double mean_subject_len, int sm_count)
+               double mean_subject_len, int sm_count, double piece_scale)
 {
     plan = SysPlan{};
     plan.piece = piece_len;
@@ -551,7 +551,12 @@ int build_plan(const std::vector<SysEntry> &entries, const std::vector<uint8_t> 
         b.nentries = (uint32_t)by_r[R].size();
         uint64_t pairs = 0;
         for (const SysEntry &e : by_r[R]) pairs += e.nsub;
-        b.piece = piece_len ? piece_len : tuned_piece(pairs, mean_subject_len, warps);
+        if (piece_len) {
+            b.piece = piece_len;
+        } else {
+            const double p = (double)tuned_piece(pairs, mean_subject_len, warps) * piece_scale;
+            b.piece = ((uint32_t)std::min(8192.0, std::max(32.0, p)) + 31u) & ~31u;
+        }
         std::vector<uint32_t> &pf = prefixes[R];
         pf.resize(b.nentries + 1);
         uint64_t acc = 0;

@@ -35,9 +35,10 @@ inline int systolic_rows(int la) { return la <= 32 ? 1 : (la + 31) / 32; }
 // with a read set) instead of stream-ordered memory.
 // piece_len == 0: each bucket's piece comes from the cost model (tuned_piece) given the
 // subjects' mean length.
+// piece_scale multiplies the cost model's piece (the batch autotuner's knob).
 int build_plan(const std::vector<SysEntry> &entries, const std::vector<uint8_t> &rows,
                SysPlan &plan, bool persistent, cudaStream_t stream, uint32_t piece_len,
-               double mean_subject_len, int sm_count);
+               double mean_subject_len, int sm_count, double piece_scale = 1.0);
 uint32_t tuned_piece(uint64_t pairs, double mean_len, int warps);
 // Number of warps the systolic kernel keeps resident on the whole GPU.
 int systolic_resident_warps(int sm_count);

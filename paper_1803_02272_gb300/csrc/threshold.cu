@@ -160,10 +160,13 @@ __device__ __forceinline__ void tri_advance(uint64_t &i, uint64_t &j, uint64_t s
 
 // The triangle as one flat stream: each warp owns a contiguous run of 256-entry spans
 // and lane l reads entries 8l .. 8l+7 of a span with one 16-byte load (the triangle must
-// be 16-byte aligned); every hit joins its two reads.
+// be 16-byte aligned).  Hits are appended to an edge list (one atomic per warp and entry
+// slot, ballot-aggregated): the unions run afterwards one edge per thread, so a warp
+// whose rows are full of hits does not serialise the latency of its unions.  Every hit
+// is counted; edges past the list's capacity are left to tri_union_kernel.
 __global__ void __launch_bounds__(256)
-tri_union_stream_kernel(const uint16_t *__restrict__ tri, const uint16_t *__restrict__ len, uint64_t n,
-                        uint64_t m, Threshold th, uint32_t *parent, unsigned long long *count)
+tri_hits_stream_kernel(const uint16_t *__restrict__ tri, const uint16_t *__restrict__ len, uint64_t n,
+                       uint64_t m, Threshold th, uint2 *edges, uint64_t cap, unsigned long long *count)
 {
     const uint64_t warp_id = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -171,44 +174,71 @@ tri_union_stream_kernel(const uint16_t *__restrict__ tri, const uint16_t *__rest
     const uint64_t spans = (m + 255) / 256;
     const uint64_t per = (spans + nwarps - 1) / nwarps;
     const uint64_t s0 = warp_id * per, s1 = min(spans, s0 + per);
-    unsigned long long local = 0;
-    if (s0 < s1) {
-        uint64_t i = 0, j = 1;
-        const uint64_t k_first = s0 * 256 + 8 * lane;
-        if (k_first < m) tri_unindex(k_first, n, i, j);
-        const uint4 *t4 = reinterpret_cast<const uint4 *>(tri);
-        for (uint64_t sp = s0; sp < s1; ++sp) {
-            const uint64_t kb = sp * 256 + 8 * lane;
-            if (kb < m) {
-                uint32_t w[4] = {0u, 0u, 0u, 0u};
-                if (kb + 8 <= m) {
-                    const uint4 v = __ldg(t4 + kb / 8);
-                    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
-                } else {
-                    for (uint64_t e = 0; kb + e < m; ++e)
-                        w[e >> 1] |= (uint32_t)tri[kb + e] << (16 * (e & 1));
-                }
-                const uint32_t li = len[i];
-                uint64_t ii = i, jj = j;
-                uint32_t lii = li;
+    if (s0 >= s1) return;                      // warp-uniform
+    uint64_t i = 0, j = 1;
+    const uint64_t k_first = s0 * 256 + 8 * lane;
+    if (k_first < m) tri_unindex(k_first, n, i, j);
+    const uint4 *t4 = reinterpret_cast<const uint4 *>(tri);
+    for (uint64_t sp = s0; sp < s1; ++sp) {
+        const uint64_t kb = sp * 256 + 8 * lane;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (kb + 8 <= m) {
+            const uint4 v = __ldg(t4 + kb / 8);
+            w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+        } else {
+            for (uint64_t e = 0; kb + e < m; ++e) w[e >> 1] |= (uint32_t)tri[kb + e] << (16 * (e & 1));
+        }
+        uint64_t ii = i, jj = j;
+        uint32_t lii = (kb < m) ? len[i] : 0u;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    if (kb + e < m) {
-                        const uint32_t d = (w[e >> 1] >> (16 * (e & 1))) & 0xffffu;
-                        if (is_hit(d, lii, len[jj], th)) {
-                            ++local;
-                            uf_union(parent, (uint32_t)ii, (uint32_t)jj);
-                        }
-                        if (++jj == n) { ++ii; jj = ii + 1; lii = len[ii < n ? ii : 0]; }
-                    }
+        for (int e = 0; e < 8; ++e) {
+            bool hit = false;
+            if (kb + e < m) {
+                const uint32_t d = (w[e >> 1] >> (16 * (e & 1))) & 0xffffu;
+                hit = is_hit(d, lii, len[jj], th);
+            }
+            const uint32_t mask = __ballot_sync(0xffffffffu, hit);
+            if (mask) {
+                unsigned long long base = 0;
+                if (lane == (uint32_t)(__ffs(mask) - 1)) base = atomicAdd(count, (unsigned long long)__popc(mask));
+                base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+                if (hit) {
+                    const unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
+                    if (slot < cap) edges[slot] = make_uint2((uint32_t)ii, (uint32_t)jj);
                 }
             }
-            tri_advance(i, j, 256, n);
+            if (kb + e < m && ++jj == n) { ++ii; jj = ii + 1; lii = len[ii < n ? ii : 0]; }
         }
+        tri_advance(i, j, 256, n);
     }
-    if (count) {
-        for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
-        if (lane == 0 && local) atomicAdd(count, local);
+}
+
+// One edge per thread.
+__global__ void union_edges_kernel(const uint2 *__restrict__ edges, uint64_t cap, const unsigned long long *count,
+                                   uint32_t *parent)
+{
+    const unsigned long long ne = *count;
+    const uint64_t e_end = ne < cap ? ne : cap;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e_end; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint2 ed = edges[e];
+        uf_union(parent, ed.x, ed.y);
+    }
+}
+
+// Rows of the triangle, each hit joined directly; with `only_if_over` it runs only when
+// the edge list overflowed (*count > cap), as the fallback for the edges it could not hold
+// (unions are idempotent, so redoing the others is harmless).
+__global__ void __launch_bounds__(256)
+tri_union_rows_kernel(const uint16_t *__restrict__ tri, const uint16_t *__restrict__ len, uint64_t n, Threshold th,
+                      uint32_t *parent, const unsigned long long *count, uint64_t cap)
+{
+    if (count && *count <= cap) return;
+    for (uint64_t i = blockIdx.x; i + 1 < n; i += gridDim.x) {
+        const uint64_t base = i * n - i * (i + 1) / 2;
+        const uint32_t li = len[i];
+        for (uint64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
+            if (is_hit(tri[base + (j - i - 1)], li, len[j], th)) uf_union(parent, (uint32_t)i, (uint32_t)j);
+        }
     }
 }
 
@@ -219,6 +249,8 @@ __global__ void flatten_kernel(uint32_t *parent, uint64_t n)
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
         parent[i] = uf_find(parent, (uint32_t)i);
 }
+
+constexpr uint64_t kEdgeCap = 64ull << 20;   // edges held between the two phases (512 MB)
 
 int grid_of(uint64_t work, int sm_count, int per_sm)
 {
@@ -256,9 +288,32 @@ int launch_tri_components(const uint16_t *tri, const DeviceReads &S, const Thres
     if (n >= 2) {
         const uint64_t m = n * (n - 1) / 2;
         if (reinterpret_cast<uintptr_t>(tri) % 16 == 0) {
-            tri_union_stream_kernel<<<grid_of((m + 255) / 256, sm_count, 8), 256, 0, st>>>(tri, S.len, n, m, th,
-                                                                                       parent, count);
-            if ((rc = check_launch("tri_union_stream_kernel launch")) != GBD_OK) return rc;
+            // edge list of up to kEdgeCap hits, then one union per edge; the row kernel
+            // takes over only if the list overflowed
+            const uint64_t cap = std::min<uint64_t>(m, kEdgeCap);
+            uint2 *edges = nullptr;
+            unsigned long long *cnt = nullptr;
+            GBD_CUDA_TRY(cudaMallocAsync((void **)&edges, cap * sizeof(uint2), st));
+            GBD_CUDA_TRY(cudaMallocAsync((void **)&cnt, sizeof(unsigned long long), st));
+            GBD_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+            tri_hits_stream_kernel<<<grid_of((m + 255) / 256, sm_count, 8), 256, 0, st>>>(tri, S.len, n, m, th, edges,
+                                                                                      cap, cnt);
+            rc = check_launch("tri_hits_stream_kernel launch");
+            if (rc == GBD_OK) {
+                union_edges_kernel<<<grid_of((cap + 255) / 256, sm_count, 16), 256, 0, st>>>(edges, cap, cnt, parent);
+                rc = check_launch("union_edges_kernel launch");
+            }
+            if (rc == GBD_OK) {
+                tri_union_rows_kernel<<<grid_of(n - 1, sm_count, 8), 256, 0, st>>>(tri, S.len, n, th, parent, cnt, cap);
+                rc = check_launch("tri_union_rows_kernel launch");
+            }
+            if (rc == GBD_OK && count) {
+                cudaError_t e = cudaMemcpyAsync(count, cnt, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync");
+            }
+            cudaFreeAsync(edges, st);
+            cudaFreeAsync(cnt, st);
+            if (rc != GBD_OK) return rc;
         } else {
             tri_union_kernel<<<grid_of(n - 1, sm_count, 8), 256, 0, st>>>(tri, S.len, n, th, parent, count);
             if ((rc = check_launch("tri_union_kernel launch")) != GBD_OK) return rc;

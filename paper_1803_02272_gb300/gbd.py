@@ -33,7 +33,7 @@ EXPORTS = [
     "gbd_batch", "gbd_server_create", "gbd_server_submit", "gbd_server_poll",
     "gbd_server_wait", "gbd_server_destroy", "gbd_last_error", "gbd_probe_op_rate",
     "gbd_kernel_launches", "gbd_tile_noalloc", "gbd_sqdist_square", "gbd_gram_apply", "gbd_mds",
-    "gbd_tile_hits", "gbd_threshold_components", "gbd_tri_components",
+    "gbd_tile_hits", "gbd_threshold_components", "gbd_tri_components", "gbd_batch_tuning",
 ]
 
 
@@ -86,6 +86,8 @@ def _declare(lib):
                            vp, vp, vp, vp], ci),
         "gbd_threshold_components": ([vp, vp, ctypes.POINTER(GbdThreshold), vp, vp, vp, vp], ci),
         "gbd_tri_components": ([vp, vp, vp, ctypes.POINTER(GbdThreshold), vp, vp, vp], ci),
+        "gbd_batch_tuning": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ci)], ci),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -185,6 +187,15 @@ def gbd_batch(ctx: int, samples, d_tris, stream=None) -> None:
     arr_o = (ctypes.c_void_p * max(ns, 1))(*[_ptr(t) for t in d_tris])
     _check(_lib.gbd_batch(ctx, ctypes.cast(arr_s, ctypes.c_void_p), ns,
                           ctypes.cast(arr_o, ctypes.c_void_p), _stream(stream)))
+
+
+def gbd_batch_tuning(ctx: int) -> dict:
+    """Autotuner state of the context's batched launch."""
+    ms = (ctypes.c_double * 3)()
+    sc = ctypes.c_double()
+    done = ctypes.c_int()
+    _check(_lib.gbd_batch_tuning(ctx, ms, ctypes.byref(sc), ctypes.byref(done)))
+    return {"trial_ms": list(ms), "piece_scale": sc.value, "done": bool(done.value)}
 
 
 def gbd_server_create(ctx: int, ref: int) -> int:

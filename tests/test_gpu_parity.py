@@ -185,6 +185,30 @@ def test_batch_matches_per_sample(gbd):
         np.testing.assert_array_equal(gbd.as_uint16(o), oracle.all_pairs(rs))
 
 
+def test_batch_autotuner(gbd):
+    """The first calls time three work-unit sizes, then the fastest is kept; every call's
+    output is exact."""
+    import torch
+    samples = synth.workload_batched(n_samples=6, n_lo=50, n_hi=400)
+    ctx = _ctx(gbd)
+    sets = [ctx.load(s) for s in samples]
+    outs = [torch.empty(max(s.n * (s.n - 1) // 2, 1), dtype=torch.int16, device="cuda") for s in samples]
+    want = [oracle.all_pairs(rs) for rs in samples]
+    states = []
+    for call in range(6):
+        for o in outs:
+            o.fill_(-1)
+        ctx.batch(sets, outs=outs)
+        torch.cuda.synchronize()
+        for rs, o, w in zip(samples, outs, want):
+            np.testing.assert_array_equal(gbd.as_uint16(o[: rs.n * (rs.n - 1) // 2]), w)
+        states.append(gbd.gbd_batch_tuning(ctx.handle))
+    assert not states[0]["done"] and states[3]["done"] and states[5]["done"]
+    t = states[5]["trial_ms"]
+    assert all(x > 0 for x in t)
+    assert states[5]["piece_scale"] == [1.0, 0.5, 2.0][int(np.argmin(t))]
+
+
 def test_batch_graph_replay_and_recapture(gbd):
     """gbd_batch records its launch group as a CUDA graph: a second call with the same
     samples and outputs replays it, other outputs re-record it; results stay exact."""
