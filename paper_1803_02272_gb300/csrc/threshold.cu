@@ -24,6 +24,14 @@ __device__ __forceinline__ bool is_hit(uint32_t d, uint32_t la, uint32_t lb, con
     return d <= th.abs_max && (uint64_t)d * th.den <= (uint64_t)th.num * L;
 }
 
+// The same test in 32-bit arithmetic, exact when num and den are below 2^16 (d and the
+// lengths are below 2^16, so both products fit).
+__device__ __forceinline__ bool is_hit32(uint32_t d, uint32_t la, uint32_t lb, const Threshold &th)
+{
+    const uint32_t L = la > lb ? la : lb;
+    return d <= th.abs_max && d * th.den <= th.num * L;
+}
+
 __device__ __forceinline__ uint32_t uf_load(const uint32_t *p)
 {
     return *reinterpret_cast<const volatile uint32_t *>(p);
@@ -162,8 +170,11 @@ __device__ __forceinline__ void tri_advance(uint64_t &i, uint64_t &j, uint64_t s
 // and lane l reads entries 8l .. 8l+7 of a span with one 16-byte load (the triangle must
 // be 16-byte aligned).  Hits are appended to an edge list (one atomic per warp and entry
 // slot, ballot-aggregated): the unions run afterwards one edge per thread, so a warp
-// whose rows are full of hits does not serialise the latency of its unions.  Every hit
-// is counted; edges past the list's capacity are left to tri_union_kernel.
+// whose rows are full of hits does not serialise the latency of its unions.  Hits are
+// rare, so each lane first tests its eight entries into a bit mask and the warp takes the
+// append path only when some lane has one.  Every hit is counted; edges past the list's
+// capacity are left to tri_union_rows_kernel.
+template <bool NARROW>
 __global__ void __launch_bounds__(256)
 tri_hits_stream_kernel(const uint16_t *__restrict__ tri, const uint16_t *__restrict__ len, uint64_t n,
                        uint64_t m, Threshold th, uint2 *edges, uint64_t cap, unsigned long long *count)
@@ -188,28 +199,54 @@ tri_hits_stream_kernel(const uint16_t *__restrict__ tri, const uint16_t *__restr
         } else {
             for (uint64_t e = 0; kb + e < m; ++e) w[e >> 1] |= (uint32_t)tri[kb + e] << (16 * (e & 1));
         }
-        uint64_t ii = i, jj = j;
-        uint32_t lii = (kb < m) ? len[i] : 0u;
+        // bit e of hmask: entry e is a hit
+        uint32_t hmask = 0;
+        {
+            uint64_t ii = i, jj = j;
+            uint32_t lii = (kb < m) ? len[i] : 0u;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            bool hit = false;
-            if (kb + e < m) {
-                const uint32_t d = (w[e >> 1] >> (16 * (e & 1))) & 0xffffu;
-                hit = is_hit(d, lii, len[jj], th);
-            }
-            const uint32_t mask = __ballot_sync(0xffffffffu, hit);
-            if (mask) {
-                unsigned long long base = 0;
-                if (lane == (uint32_t)(__ffs(mask) - 1)) base = atomicAdd(count, (unsigned long long)__popc(mask));
-                base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
-                if (hit) {
-                    const unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
-                    if (slot < cap) edges[slot] = make_uint2((uint32_t)ii, (uint32_t)jj);
+            for (int e = 0; e < 8; ++e) {
+                if (kb + e < m) {
+                    const uint32_t d = (w[e >> 1] >> (16 * (e & 1))) & 0xffffu;
+                    const uint32_t lj = len[jj];
+                    if (NARROW ? is_hit32(d, lii, lj, th) : is_hit(d, lii, lj, th)) hmask |= 1u << e;
+                    if (++jj == n) { ++ii; jj = ii + 1; lii = len[ii < n ? ii : 0]; }
                 }
             }
-            if (kb + e < m && ++jj == n) { ++ii; jj = ii + 1; lii = len[ii < n ? ii : 0]; }
+        }
+        if (__any_sync(0xffffffffu, hmask != 0)) {
+            uint64_t ii = i, jj = j;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const bool hit = (hmask >> e) & 1u;
+                const uint32_t mask = __ballot_sync(0xffffffffu, hit);
+                if (mask) {
+                    unsigned long long base = 0;
+                    if (lane == (uint32_t)(__ffs(mask) - 1)) base = atomicAdd(count, (unsigned long long)__popc(mask));
+                    base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+                    if (hit) {
+                        const unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
+                        if (slot < cap) edges[slot] = make_uint2((uint32_t)ii, (uint32_t)jj);
+                    }
+                }
+                if (kb + e < m && ++jj == n) { ++ii; jj = ii + 1; }
+            }
         }
         tri_advance(i, j, 256, n);
+    }
+}
+
+// Hooks every read of an edge's larger end under its smallest neighbour (atomicMin):
+// a valid starting forest (links point to smaller reads of the same component) that
+// leaves the unions little to do.
+__global__ void min_hook_kernel(const uint2 *__restrict__ edges, uint64_t cap, const unsigned long long *count,
+                                uint32_t *parent)
+{
+    const unsigned long long ne = *count;
+    const uint64_t e_end = ne < cap ? ne : cap;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e_end; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint2 ed = edges[e];            // ed.x < ed.y
+        atomicMin(parent + ed.y, ed.x);
     }
 }
 
@@ -296,9 +333,16 @@ int launch_tri_components(const uint16_t *tri, const DeviceReads &S, const Thres
             GBD_CUDA_TRY(cudaMallocAsync((void **)&edges, cap * sizeof(uint2), st));
             GBD_CUDA_TRY(cudaMallocAsync((void **)&cnt, sizeof(unsigned long long), st));
             GBD_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
-            tri_hits_stream_kernel<<<grid_of((m + 255) / 256, sm_count, 8), 256, 0, st>>>(tri, S.len, n, m, th, edges,
-                                                                                      cap, cnt);
+            const int grid = grid_of((m + 255) / 256, sm_count, 8);
+            if (th.num < 65536u && th.den < 65536u)
+                tri_hits_stream_kernel<true><<<grid, 256, 0, st>>>(tri, S.len, n, m, th, edges, cap, cnt);
+            else
+                tri_hits_stream_kernel<false><<<grid, 256, 0, st>>>(tri, S.len, n, m, th, edges, cap, cnt);
             rc = check_launch("tri_hits_stream_kernel launch");
+            if (rc == GBD_OK) {
+                min_hook_kernel<<<grid_of((cap + 255) / 256, sm_count, 16), 256, 0, st>>>(edges, cap, cnt, parent);
+                rc = check_launch("min_hook_kernel launch");
+            }
             if (rc == GBD_OK) {
                 union_edges_kernel<<<grid_of((cap + 255) / 256, sm_count, 16), 256, 0, st>>>(edges, cap, cnt, parent);
                 rc = check_launch("union_edges_kernel launch");
