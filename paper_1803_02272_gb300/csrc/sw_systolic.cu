@@ -109,9 +109,11 @@ struct SysUnit {
     uint32_t job, q, sub_begin, nsub;
 };
 
-// Warp-uniform cursor over one half's subject stream.
+// Warp-uniform cursor over one half's subject stream.  rem = bases of the current subject
+// from the current chunk on; wp = the subject's packed words.
 struct Cursor {
-    uint32_t pos, cnt, ck, nck, orig, len, next_orig, next_len;
+    uint32_t pos, cnt, ck, rem, len, next_orig, next_len;
+    const uint32_t *wp;
 };
 
 __device__ __forceinline__ void subject_at(const SysJob &J, uint32_t list_index, uint32_t &orig,
@@ -121,19 +123,16 @@ __device__ __forceinline__ void subject_at(const SysJob &J, uint32_t list_index,
     len = __ldg(J.S.len + orig);
 }
 
-__device__ __forceinline__ uint32_t nchunks(uint32_t len) { return len == 0 ? 1u : (len + 15u) >> 4; }
-
 __device__ __forceinline__ void cursor_init(Cursor &cu, const SysJob &J, const SysUnit &u, int h)
 {
     cu.cnt = (u.nsub + 1 - h) >> 1;            // half h takes list positions h, h+2, ...
     cu.pos = 0;
     cu.ck = 0;
-    if (cu.cnt > 0) {
-        subject_at(J, u.sub_begin + h, cu.orig, cu.len);
-        cu.nck = nchunks(cu.len);
-    } else {
-        cu.orig = 0; cu.len = 0; cu.nck = 0xffffffffu;
-    }
+    uint32_t orig = 0;
+    cu.len = 0;
+    if (cu.cnt > 0) subject_at(J, u.sub_begin + h, orig, cu.len);
+    cu.rem = cu.len;
+    cu.wp = J.S.words + (uint64_t)orig * J.S.stride;
     if (cu.cnt > 1) subject_at(J, u.sub_begin + h + 2, cu.next_orig, cu.next_len);
     else { cu.next_orig = 0; cu.next_len = 0; }
 }
@@ -141,17 +140,17 @@ __device__ __forceinline__ void cursor_init(Cursor &cu, const SysJob &J, const S
 __device__ __forceinline__ void cursor_advance(Cursor &cu, const SysJob &J, const SysUnit &u, int h)
 {
     if (cu.pos >= cu.cnt) return;
-    if (++cu.ck < cu.nck) return;
+    ++cu.ck;
+    if (cu.rem > 16u) {                        // another chunk of the same subject
+        cu.rem -= 16u;
+        return;
+    }
     cu.ck = 0;
     ++cu.pos;
-    cu.orig = cu.next_orig;
     cu.len = cu.next_len;
-    if (cu.pos < cu.cnt) {
-        cu.nck = nchunks(cu.len);
-        if (cu.pos + 1 < cu.cnt) subject_at(J, u.sub_begin + h + 2 * (cu.pos + 1), cu.next_orig, cu.next_len);
-    } else {
-        cu.nck = 0xffffffffu;
-    }
+    cu.rem = cu.next_len;
+    cu.wp = J.S.words + (uint64_t)cu.next_orig * J.S.stride;
+    if (cu.pos + 1 < cu.cnt) subject_at(J, u.sub_begin + h + 2 * (cu.pos + 1), cu.next_orig, cu.next_len);
 }
 
 // Stream metadata + packed word of the chunk a cursor points at.
@@ -159,43 +158,37 @@ struct ChunkInfo {
     uint32_t word;      // 16 bases, 2 bits each
     uint32_t nvalid;    // valid columns in this chunk (0 = padding chunk)
     uint32_t first, last;
-    uint32_t orig, len, pos;
+    uint32_t len, pos;
 };
 
 __device__ __forceinline__ void cursor_chunk(const Cursor &cu, const SysJob &J, ChunkInfo &ci)
 {
     const bool valid = cu.pos < cu.cnt;
     ci.first = valid && cu.ck == 0;
-    ci.last = valid && cu.ck + 1 == cu.nck;
-    ci.orig = cu.orig;
+    ci.last = valid && cu.rem <= 16u;          // an empty subject is one padding chunk
     ci.pos = cu.pos;
     ci.len = cu.len;
-    if (valid) {
-        const uint32_t base = cu.ck * 16u;
-        ci.nvalid = cu.len > base ? min(16u, cu.len - base) : 0u;
-        ci.word = __ldg(J.S.words + (uint64_t)cu.orig * J.S.stride + cu.ck);
-    } else {
-        ci.nvalid = 0;
-        ci.word = 0;
-    }
+    ci.nvalid = valid ? min(16u, cu.rem) : 0u;
+    ci.word = valid ? __ldg(cu.wp + cu.ck) : 0u;
 }
 
 // Write chunk X of the two half streams into the warp's profile ring and table.
-// m = X mod RING_CHUNKS, the ring slot of stream chunk X.
+// m = X mod RING_CHUNKS, the ring slot of stream chunk X.  Both halves at once: the two
+// base codes of this lane's column sit in the halves of one word, a half equal to the
+// query base q gives s + 2 = 3, any other 1, a padding column the never-matching value.
 __device__ __forceinline__ void fill_chunk(uint32_t *ws, int lane, int m, const ChunkInfo &lo,
                                            const ChunkInfo &hi)
 {
     const int x = lane & 15;
     const int qa = (lane >> 4) * 2;
-    const uint32_t blo = (lo.word >> (2 * x)) & 3u, bhi = (hi.word >> (2 * x)) & 3u;
-    const bool vlo = (uint32_t)x < lo.nvalid, vhi = (uint32_t)x < hi.nvalid;
+    const uint32_t codes = ((lo.word >> (2 * x)) & 3u) | (((hi.word >> (2 * x)) & 3u) << 16);
+    const uint32_t pad = ((uint32_t)x < lo.nvalid ? 0u : 0x0000ffffu) | ((uint32_t)x < hi.nvalid ? 0u : 0xffff0000u);
     const int rho = 16 * m + x;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
         const uint32_t q = (uint32_t)(qa + t);
-        const uint32_t slo = vlo ? (blo == q ? 3u : 1u) : 0xC000u;
-        const uint32_t shi = vhi ? (bhi == q ? 3u : 1u) : 0xC000u;
-        const uint32_t v = slo | (shi << 16);
+        const uint32_t ne = __vminu2(codes ^ (q * ONE2), ONE2);   // 0 where the base matches, else 1
+        const uint32_t v = lop_sel(0x00030003u - ne - ne, NEG2, pad);
         uint32_t *arr = ws + q * PWORDS;
         arr[pslot(rho)] = v;
         if (rho < 32) arr[pslot(rho + RING)] = v;
@@ -380,7 +373,7 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
         {
             uint32_t recv = __shfl_up_sync(0xffffffffu, emit, 1);
             if (lane == 0) recv = 0;
-            const uint32_t negfb = pack2(-(int)(fbase & 0xffffu));
+            const uint32_t negfb = __vsub2(0u, fbase);                 // -fbase in both halves
             const uint32_t a = vaddmax(prevRel, negfb, acc);       // max(acc, prev - fbase)
             const uint32_t total = vmax2(a, recv);
             emit = lop_sel(emit, total, Mend);
