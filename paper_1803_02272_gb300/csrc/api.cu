@@ -49,12 +49,14 @@ Scoring scoring_of(const gbd_ctx *ctx)
             ctx->params.gap_open};
 }
 
+// The systolic kernel is specialised to match +1, mismatch -1, gap extension 1; it takes
+// a gap opening penalty up to kSystolicMaxGapOpen (0 = linear gaps).
 static bool default_scores(const gbd_params &p)
 {
-    return p.match == 1 && p.mismatch == -1 && p.gap == 1 && p.gap_open == 0;
+    return p.match == 1 && p.mismatch == -1 && p.gap == 1 && p.gap_open >= 0 &&
+           p.gap_open <= kSystolicMaxGapOpen;
 }
 
-// The systolic kernel is specialised to the default scores.
 static bool use_systolic(const gbd_ctx *ctx)
 {
     return ctx->params.kernel != GBD_KERNEL_GENERAL && default_scores(ctx->params);
@@ -134,9 +136,10 @@ static int all_pairs_systolic(gbd_ctx *ctx, gbd_set *set, uint16_t *d_tri, cudaS
     job.n = set->n;
     job.mode = OUT_TRI;
     job.conversion = ctx->params.conversion;
+    job.gap_open = ctx->params.gap_open;
     SysJob *d_job = nullptr;
     if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
-    rc = run_systolic(d_job, sc.plan, ctx->sm_count, st, ctx->aux, ctx->fork, ctx->join);
+    rc = run_systolic(d_job, sc.plan, ctx->sm_count, st, ctx->aux, ctx->fork, ctx->join, job.gap_open > 0);
     cudaFreeAsync(d_job, st);
     if (rc != GBD_OK) return rc;
     return long_rows_general(ctx, set, d_tri, st);
@@ -182,12 +185,13 @@ static int tile_impl(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, c
         job.col0 = b0;
         job.mode = OUT_RECT;
         job.conversion = ctx->params.conversion;
+        job.gap_open = ctx->params.gap_open;
         SysJob *d_job = nullptr;
         SysPlan plan;
         if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
         if ((rc = build_plan(entries, rows, plan, false, st, 0, B->mean_len, ctx->sm_count)) != GBD_OK)
             return rc;
-        rc = run_systolic(d_job, plan, ctx->sm_count, st, ctx->aux, ctx->fork, ctx->join);
+        rc = run_systolic(d_job, plan, ctx->sm_count, st, ctx->aux, ctx->fork, ctx->join, job.gap_open > 0);
         cudaFreeAsync(d_job, st);
         free_plan(plan, st);
         if (rc != GBD_OK) return rc;
@@ -238,9 +242,10 @@ struct BatchGraph {
     double trial_ms[kTrials] = {0, 0, 0};
     double scale = 1.0;               // piece scale of the current graph
     cudaEvent_t t0 = nullptr, t1 = nullptr;
-    bool matches(const gbd_set *const *samples, uint64_t ns, uint16_t *const *d_tris, int conv) const
+    int gap_open = 0;
+    bool matches(const gbd_set *const *samples, uint64_t ns, uint16_t *const *d_tris, int conv, int go) const
     {
-        if (ids.size() != ns || conversion != conv) return false;
+        if (ids.size() != ns || conversion != conv || gap_open != go) return false;
         for (uint64_t s = 0; s < ns; ++s)
             if (ids[s] != samples[s]->id || outs[s] != d_tris[s]) return false;
         return true;
@@ -286,6 +291,7 @@ static int capture_batch(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const *sam
         job.n = set->n;
         job.mode = OUT_TRI;
         job.conversion = ctx->params.conversion;
+        job.gap_open = ctx->params.gap_open;
         for (uint64_t i = 0; i + 1 < set->n; ++i) {
             if (set->h_len[i] > kSystolicMaxQuery) continue;
             entries.push_back({(uint32_t)s, (uint32_t)i, (uint32_t)(i + 1), (uint32_t)(set->n - 1 - i)});
@@ -295,6 +301,7 @@ static int capture_batch(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const *sam
         n_sum += (double)set->n;
     }
     bg->conversion = ctx->params.conversion;
+    bg->gap_open = ctx->params.gap_open;
     {
         std::vector<size_t> order(entries.size());
         std::iota(order.begin(), order.end(), 0);
@@ -332,7 +339,8 @@ static int record_batch_graph(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const
     if (rc != GBD_OK) return rc;
     const uint64_t launches0 = gbd_kernel_launches();
     GBD_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    rc = run_systolic(bg->d_jobs, bg->plan, ctx->sm_count, cap, ctx->aux, ctx->fork, ctx->join);
+    rc = run_systolic(bg->d_jobs, bg->plan, ctx->sm_count, cap, ctx->aux, ctx->fork, ctx->join,
+                      ctx->params.gap_open > 0);
     for (uint64_t s = 0; s < ns && rc == GBD_OK; ++s) rc = long_rows_general(ctx, samples[s], d_tris[s], cap);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cap, &g);
@@ -383,8 +391,8 @@ int gbd_create(gbd_ctx **out, int device, const gbd_params *p)
     if (prm.kernel < GBD_KERNEL_AUTO || prm.kernel > GBD_KERNEL_SYSTOLIC)
         return fail(GBD_EINVAL, "gbd_create: unknown kernel choice");
     if (prm.kernel == GBD_KERNEL_SYSTOLIC && !default_scores(prm))
-        return fail(GBD_EINVAL, "gbd_create: the systolic kernel supports the default scores "
-                                "(+1/-1/gap 1) only");
+        return fail(GBD_EINVAL, "gbd_create: the systolic kernel supports match +1, mismatch -1, gap "
+                                "extension 1 and a gap opening penalty up to 1000 only");
     int ndev = 0;
     GBD_CUDA_TRY(cudaGetDeviceCount(&ndev));
     if (device < 0 || device >= ndev) return fail(GBD_EINVAL, "gbd_create: no such device");
@@ -676,7 +684,7 @@ int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns, uint16_t
     if (rc != GBD_OK) return rc;
     BatchGraph *bg = static_cast<BatchGraph *>(ctx->batch_cache);
     bool fresh = false;
-    if (!(bg && bg->matches(samples, ns, d_tris, ctx->params.conversion))) {
+    if (!(bg && bg->matches(samples, ns, d_tris, ctx->params.conversion, ctx->params.gap_open))) {
         free_batch_cache(ctx);
         bg = new BatchGraph();
         ctx->batch_cache = bg;

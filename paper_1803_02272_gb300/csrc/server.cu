@@ -107,7 +107,8 @@ bool valid_base(uint8_t c)
 
 bool use_systolic_scores(const gbd_params &p)
 {
-    return p.kernel != GBD_KERNEL_GENERAL && p.match == 1 && p.mismatch == -1 && p.gap == 1 && p.gap_open == 0;
+    return p.kernel != GBD_KERNEL_GENERAL && p.match == 1 && p.mismatch == -1 && p.gap == 1 && p.gap_open >= 0 &&
+           p.gap_open <= kSystolicMaxGapOpen;
 }
 
 // Called with srv->mu held: one chunk of r finished (or failed with `err`).
@@ -196,6 +197,7 @@ std::string launch_batch(gbd_server *srv, const std::vector<Piece> &pieces, cuda
         J.col0 = 0;
         J.mode = OUT_RECT;
         J.conversion = ctx->params.conversion;
+        J.gap_open = ctx->params.gap_open;
         const uint32_t job = (uint32_t)jobs.size();
         jobs.push_back(J);
         std::vector<uint32_t> long_rows;
@@ -242,7 +244,8 @@ std::string launch_batch(gbd_server *srv, const std::vector<Piece> &pieces, cuda
                      ctx->params.gap_open};
     for (const GeneralJob &gj : general)
         if (err.empty() && run_general(gj, sc, ctx->sm_count, st) != GBD_OK) err = gbd_last_error();
-    if (err.empty() && !entries.empty() && run_systolic(d_jobs, plan, ctx->sm_count, st) != GBD_OK)
+    if (err.empty() && !entries.empty() &&
+        run_systolic(d_jobs, plan, ctx->sm_count, st, nullptr, nullptr, nullptr, ctx->params.gap_open > 0) != GBD_OK)
         err = gbd_last_error();
     plan.stream_ordered = true;
     free_plan(plan, st);

@@ -208,7 +208,7 @@ __device__ __forceinline__ uint2 lds64(const uint32_t *ws_words, uint32_t byte_o
     return *reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(ws_words) + byte_off);
 }
 
-template <int R>
+template <int R, bool AFFINE>
 __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint32_t *ws, int lane,
                                       int neg_rel, uint32_t *err)
 {
@@ -260,6 +260,21 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
     uint32_t hist[HIST ? CH : 1];
 #pragma unroll
     for (int i = 0; i < (HIST ? CH : 1); ++i) hist[i] = f_prev;
+    // Affine gaps (open `gap_open`, extend 1), in the same bias: Eh = E + f carries a
+    // horizontal gap along each row, Fh = F + f a vertical one down the column,
+    //   Eh = max(Eh_left, K_left - gap_open), Fh = max(Fh_up, K_up - gap_open),
+    //   K = max(f, K_diag + s + 2, Eh, Fh);
+    // minus infinity is NEG2.  Fh of a lane's last row reaches the next lane like K does
+    // (histF when D > 0).
+    constexpr int NA = AFFINE ? R : 1;
+    constexpr bool HISTF = AFFINE && HIST;
+    uint32_t Eh[NA], Fh[NA];
+    uint32_t histF[HISTF ? CH : 1];
+#pragma unroll
+    for (int r = 0; r < NA; ++r) { Eh[r] = NEG2; Fh[r] = NEG2; }
+#pragma unroll
+    for (int i = 0; i < (HISTF ? CH : 1); ++i) histF[i] = NEG2;
+    const uint32_t ngo = AFFINE ? pack2(-(int)J.gap_open) : 0u;
     uint32_t up0_prev = f_prev2;               // row 0's diagonal input
     uint32_t curRel = 0, prevRel = 0, acc = 0, emit = 0;
     uint32_t Mlast_prev = 0;                   // "ends a subject" masks of chunk c-1
@@ -293,6 +308,12 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
             for (int i = 0; i < (HIST ? CH : 1); ++i) hist[i] -= REBASE2;
             up0_prev -= REBASE2; f_prev -= REBASE2; f_prev2 -= REBASE2;
             prevRel -= REBASE2;               // curRel is 0 (minus infinity) here
+            if (AFFINE) {                     // saturating: minus infinity stays very negative
+#pragma unroll
+                for (int r = 0; r < NA; ++r) { Eh[r] = __vsubss2(Eh[r], REBASE2); Fh[r] = __vsubss2(Fh[r], REBASE2); }
+#pragma unroll
+                for (int i = 0; i < (HISTF ? CH : 1); ++i) histF[i] = __vsubss2(histF[i], REBASE2);
+            }
         }
 
         // ---- this lane's chunk c: stream metadata
@@ -318,6 +339,11 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
             uint32_t up0 = __shfl_up_sync(0xffffffffu,
                                           HIST ? hist[(q + CH - 1 - D) & (CH - 1)] : cur[R - 1], 1);
             if (lane == 0) up0 = f_prev;              // top boundary: H(0, j) = 0
+            uint32_t fup0 = 0u;
+            if (AFFINE) {
+                fup0 = __shfl_up_sync(0xffffffffu, HISTF ? histF[(q + CH - 1 - D) & (CH - 1)] : Fh[R - 1], 1);
+                if (lane == 0) fup0 = NEG2;           // F(0, j) = minus infinity
+            }
             uint32_t diag0 = up0_prev;
 #pragma unroll
             for (int r = R - 1; r >= 0; --r) {
@@ -329,13 +355,23 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
                     // row 0, its diagonal) become the floor of column 0.  Rows below
                     // already read the old value as their "up" input this step.
                     left = lop_sel(left, f_prev, Mfirst);
+                    if (AFFINE) Eh[r] = lop_sel(Eh[r], NEG2, Mfirst);      // E(i, 0) = -inf
                     if (r == 0) diag0 = lop_sel(diag0, f_prev2, Mfirst);
                 }
                 const uint32_t up = r ? cur[r - 1] : up0;
                 const uint32_t dg = r ? nxt[r - 1] : diag0;
                 const uint32_t s2 = (((q - r) & 1) == 0) ? sp[r].x : sp[r].y;
                 const uint32_t E = vaddmax(dg, s2, f);
-                out = vmax3(up, left, E);
+                if (AFFINE) {
+                    const uint32_t fu = r ? Fh[r - 1] : fup0;
+                    const uint32_t eh = vaddmax(left, ngo, Eh[r]);
+                    const uint32_t fh = vaddmax(up, ngo, fu);
+                    out = vmax3(E, eh, fh);
+                    Eh[r] = eh;
+                    if (HISTF && r == R - 1) histF[q] = fh; else Fh[r] = fh;
+                } else {
+                    out = vmax3(up, left, E);
+                }
                 if (((q - r) & 1) != 0) sp[r] = lds64(ws, addr[r] + 4 * poff(q + 1 - r));
             }
             up0_prev = up0;
@@ -417,8 +453,8 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
     }
 }
 
-template <int R>
-__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, BLOCKS_PER_SM)
+template <int R, bool AFFINE>
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, (AFFINE && R > 12) ? BLOCKS_PER_SM - 1 : BLOCKS_PER_SM)
 sw_systolic_kernel(const SysJob *__restrict__ jobs, const SysEntry *__restrict__ entries,
                    const uint32_t *__restrict__ prefix, uint32_t nentries, uint32_t nunits,
                    uint32_t piece_len, uint32_t *counter, uint32_t *err)
@@ -448,36 +484,37 @@ sw_systolic_kernel(const SysJob *__restrict__ jobs, const SysEntry *__restrict__
         u.q = en.q;
         u.sub_begin = en.sub_begin + piece * piece_len;
         u.nsub = min(piece_len, en.nsub - piece * piece_len);
-        run_unit<R>(jobs[u.job], u, ws, lane, neg_rel, err);
+        run_unit<R, AFFINE>(jobs[u.job], u, ws, lane, neg_rel, err);
         __syncwarp();
     }
 }
 
 // Blocks per SM of each instantiation (set up before any launch or capture).
-int g_per_sm[17];
+int g_per_sm[2][17];
 
-template <int R>
+template <int R, bool AFFINE>
 int prepare_bucket()
 {
     const size_t smem = systolic_smem_bytes();
-    GBD_CUDA_TRY(cudaFuncSetAttribute(sw_systolic_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GBD_CUDA_TRY(cudaFuncSetAttribute(sw_systolic_kernel<R, AFFINE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-    GBD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_per_sm[R], sw_systolic_kernel<R>,
+    int &bps = g_per_sm[AFFINE ? 1 : 0][R];
+    GBD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sw_systolic_kernel<R, AFFINE>,
                                                                 WARPS_PER_BLOCK * 32, smem));
-    if (g_per_sm[R] < 1) return fail(GBD_ECUDA, "systolic kernel does not fit on an SM");
+    if (bps < 1) return fail(GBD_ECUDA, "systolic kernel does not fit on an SM");
     return GBD_OK;
 }
 
-template <int R>
+template <int R, bool AFFINE>
 int launch_bucket(const SysJob *d_jobs, const SysEntry *entries, const uint32_t *prefix,
                   uint32_t nentries, uint32_t nunits, uint32_t piece_len, uint32_t *counter,
                   uint32_t *err, int sm_count, cudaStream_t stream)
 {
     const size_t smem = systolic_smem_bytes();
-    uint64_t blocks = (uint64_t)sm_count * g_per_sm[R];
+    uint64_t blocks = (uint64_t)sm_count * g_per_sm[AFFINE ? 1 : 0][R];
     const uint64_t need = (nunits + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
     if (blocks > need) blocks = need;
-    sw_systolic_kernel<R><<<(unsigned)blocks, WARPS_PER_BLOCK * 32, smem, stream>>>(
+    sw_systolic_kernel<R, AFFINE><<<(unsigned)blocks, WARPS_PER_BLOCK * 32, smem, stream>>>(
         d_jobs, entries, prefix, nentries, nunits, piece_len, counter, err);
     note_launches(1);
     cudaError_t le = cudaGetLastError();
@@ -496,7 +533,7 @@ int systolic_prepare()
     std::lock_guard<std::mutex> lk(mu);
     if (done) return GBD_OK;
     int rc = GBD_OK;
-#define GBD_CASE(RR) if (rc == GBD_OK) rc = prepare_bucket<RR>();
+#define GBD_CASE(RR) if (rc == GBD_OK) rc = prepare_bucket<RR, false>(); if (rc == GBD_OK) rc = prepare_bucket<RR, true>();
     GBD_CASE(1) GBD_CASE(2) GBD_CASE(3) GBD_CASE(4) GBD_CASE(5) GBD_CASE(6) GBD_CASE(7)
     GBD_CASE(8) GBD_CASE(9) GBD_CASE(10) GBD_CASE(11) GBD_CASE(12) GBD_CASE(13)
     GBD_CASE(14) GBD_CASE(15) GBD_CASE(16)
@@ -594,7 +631,7 @@ void free_plan(SysPlan &plan, cudaStream_t stream)
 }
 
 int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaStream_t stream,
-                 cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join)
+                 cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join, bool affine)
 {
     if (plan.buckets.empty()) return GBD_OK;
     int prc = systolic_prepare();
@@ -620,7 +657,8 @@ int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaSt
         uint32_t *ctr = scratch + 2 * i, *err = scratch + 2 * i + 1;
         cudaStream_t st = (two && (i & 1)) ? aux : stream;
         switch (b.R) {
-#define GBD_CASE(RR) case RR: rc = launch_bucket<RR>(d_jobs, en, pf, b.nentries, b.nunits, b.piece, ctr, err, sm_count, st); break;
+#define GBD_CASE(RR) case RR: rc = affine ? launch_bucket<RR, true>(d_jobs, en, pf, b.nentries, b.nunits, b.piece, ctr, err, sm_count, st) \
+                                         : launch_bucket<RR, false>(d_jobs, en, pf, b.nentries, b.nunits, b.piece, ctr, err, sm_count, st); break;
             GBD_CASE(1) GBD_CASE(2) GBD_CASE(3) GBD_CASE(4) GBD_CASE(5) GBD_CASE(6) GBD_CASE(7)
             GBD_CASE(8) GBD_CASE(9) GBD_CASE(10) GBD_CASE(11) GBD_CASE(12) GBD_CASE(13)
             GBD_CASE(14) GBD_CASE(15) GBD_CASE(16)

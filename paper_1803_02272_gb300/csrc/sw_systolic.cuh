@@ -19,6 +19,7 @@ struct SysJob {
     uint64_t ld, row0, col0;    // OUT_RECT: out[(q-row0)*ld + (s-col0)]
     int mode;                   // OUT_TRI or OUT_RECT
     int conversion;
+    int gap_open;               // affine gaps (extend 1) when > 0; launch with affine = true
 };
 
 // One query (original index q in Q, length <= 512) against the subjects at list
@@ -46,8 +47,12 @@ void free_plan(SysPlan &plan, cudaStream_t stream);
 
 // aux: optional second stream; consecutive buckets alternate between the two, forking
 // and joining on the events fork / join (owned by the caller; needed when aux is set).
+// affine: the jobs use affine gaps (every job of the launch the same way).
 int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaStream_t stream,
-                 cudaStream_t aux = nullptr, cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
+                 cudaStream_t aux = nullptr, cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr,
+                 bool affine = false);
+// Largest gap opening penalty the systolic kernel takes (its int16 values stay in range).
+constexpr int kSystolicMaxGapOpen = 1000;
 size_t systolic_smem_bytes();
 // Sets kernel attributes and occupancy of every instantiation (once; before any capture).
 int systolic_prepare();

@@ -167,11 +167,29 @@ def test_affine_gaps_exact(gbd, scores):
     np.testing.assert_array_equal(got2.astype(np.int64), want2)
 
 
-def test_affine_gap_rejected_by_systolic_and_negative(gbd):
+def test_affine_gap_limits(gbd):
+    _ctx(gbd, "systolic", gap_open=1000)            # the systolic kernel's largest opening
     with pytest.raises(gbd.GbdError):
-        _ctx(gbd, "systolic", gap_open=2)
+        _ctx(gbd, "systolic", gap_open=1001)
     with pytest.raises(gbd.GbdError):
         _ctx(gbd, "auto", gap_open=-1)
+
+
+@pytest.mark.parametrize("go", [2, 7])
+def test_affine_systolic_batch_and_tile(gbd, go):
+    """Affine gaps on the systolic kernel through the batched launch and a rectangle."""
+    import torch
+    samples = synth.workload_batched(n_samples=4, n_lo=20, n_hi=150)
+    ctx = _ctx(gbd, "systolic", gap_open=go)
+    sets = [ctx.load(s) for s in samples]
+    outs = ctx.batch(sets)
+    torch.cuda.synchronize()
+    for rs, o in zip(samples, outs):
+        np.testing.assert_array_equal(gbd.as_uint16(o), oracle.all_pairs(rs, gap_open=go))
+    A, B = samples[0], samples[1]
+    out = ctx.tile(sets[0], 0, A.n, sets[1], 0, B.n)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(gbd.as_uint16(out), oracle.rect(A, 0, A.n, B, 0, B.n, gap_open=go))
 
 
 def test_batch_matches_per_sample(gbd):
@@ -254,9 +272,11 @@ def test_10k_workload_sampled(gbd):
         np.testing.assert_array_equal(tri[kk], oracle.pairs(rs, ii, jj))
 
 
-def test_systolic_every_rows_per_lane():
+@pytest.mark.parametrize("go", [0, 2, 9])
+def test_systolic_every_rows_per_lane(go):
     """Query lengths 1..512 cover every rows-per-lane variant (R = 1..16) of the
-    systolic kernel, with subjects shorter and longer than the query."""
+    systolic kernel, with subjects shorter and longer than the query; linear gaps
+    (go = 0) and affine gaps."""
     import torch
     from paper_1803_02272_gb300 import gbd as g
     st = synth.Stream(8080, 0)
@@ -266,12 +286,13 @@ def test_systolic_every_rows_per_lane():
     base = reads[-1]
     reads += [base[5:300], base[:128] + "ACGT" * 10, base[200:]]
     rs = synth.from_strings(reads)
-    ctx = _ctx(g, "systolic")
+    ctx = _ctx(g, "systolic", gap_open=go)
     got = _all_pairs(g, ctx, rs)
-    np.testing.assert_array_equal(got, oracle.all_pairs(rs))
+    np.testing.assert_array_equal(got, oracle.all_pairs(rs, gap_open=go))
 
 
-def test_long_subject_rebases():
+@pytest.mark.parametrize("go", [0, 3])
+def test_long_subject_rebases(go):
     """A 20,000-base subject streams past short queries: the DP values are rebased many
     times inside one subject."""
     import torch
@@ -280,8 +301,10 @@ def test_long_subject_rebases():
     long = "".join("ACGT"[c] for c in synth.random_codes(st, (20000,)))
     reads = [long[1000:1300], long[15000:15450], long[19900:], "ACGT" * 50, long]
     rs = synth.from_strings(reads)
-    got = _all_pairs(g, _ctx(g, "auto"), rs)
-    np.testing.assert_array_equal(got, oracle.all_pairs(rs))
+    got = _all_pairs(g, _ctx(g, "auto", gap_open=go), rs)
+    np.testing.assert_array_equal(got, oracle.all_pairs(rs, gap_open=go))
+    if go:
+        return
     ctx = _ctx(g, "auto")
     A = ctx.load(rs.subset([0, 1, 2, 3]))
     B = ctx.load(rs.subset([4, 4, 0]))

@@ -125,3 +125,21 @@ def test_bad_request_rejected(env):
         srv.submit(synth.from_strings(["ACGTN"]))
     assert ei.value.code == gbd.GBD_EINVAL
     srv.close()
+
+
+def test_affine_server_rows_match_oracle(env):
+    """A server on a context with affine gaps (systolic kernel, gap open 3)."""
+    import torch
+    gbd, _, _, ref_rs = env
+    ctx = gbd.Context(0, gap_open=3)
+    sub = ref_rs.subset(range(400))
+    ref = ctx.load(sub)
+    srv = gbd.Server(ctx, ref)
+    q = _queries(11, [6])[0]
+    t, out = srv.submit(q)
+    srv.wait(t)
+    torch.cuda.synchronize()
+    got = gbd.as_uint16(out)
+    want = oracle.rect(q, 0, q.n, sub, 0, sub.n, gap_open=3)
+    np.testing.assert_array_equal(got, want)
+    srv.close()
