@@ -182,6 +182,14 @@ int gbd_tile_hits(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, cons
                   uint32_t *d_hits, uint64_t hit_capacity, uint64_t *d_hit_count,
                   const int32_t *d_ref_labels, int32_t *d_row_labels, void *stream);
 
+/* The same epilogue over a rectangle already computed (d_rect[(r-a0)*ld + (c-b0)] =
+ * d(A[r], B[c]), device): one streaming pass, so several thresholds or label sets can be
+ * applied without recomputing distances.  Outputs and errors as for gbd_tile_hits. */
+int gbd_rect_hits(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd_set *B, uint64_t b0,
+                  uint64_t b1, const uint16_t *d_rect, uint64_t ld, const gbd_threshold *th, uint32_t *d_hits,
+                  uint64_t hit_capacity, uint64_t *d_hit_count, const int32_t *d_ref_labels, int32_t *d_row_labels,
+                  void *stream);
+
 /* Connected components of the threshold graph of a read set (section 5: vertices are the
  * reads, an edge joins i < j when the pair is a hit).  d_labels (device, n uint32):
  * the smallest read index of each read's component.  d_edges (device, one uint64, may be

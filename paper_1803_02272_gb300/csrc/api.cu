@@ -636,6 +636,30 @@ int gbd_threshold_components(gbd_ctx *ctx, const gbd_set *set, const gbd_thresho
     return rc;
 }
 
+int gbd_rect_hits(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd_set *B, uint64_t b0,
+                  uint64_t b1, const uint16_t *d_rect, uint64_t ld, const gbd_threshold *th, uint32_t *d_hits,
+                  uint64_t hit_capacity, uint64_t *d_hit_count, const int32_t *d_ref_labels, int32_t *d_row_labels,
+                  void *stream)
+{
+    if (!ctx || !A || !B) return fail(GBD_EINVAL, "gbd_rect_hits: NULL context or set");
+    int rc = check_threshold(th);
+    if (rc != GBD_OK) return rc;
+    if (a0 > a1 || a1 > A->n || b0 > b1 || b1 > B->n)
+        return fail(GBD_EINVAL, "gbd_rect_hits: row or column range outside the sets");
+    if (a1 > a0 && b1 > b0 && (!d_rect || ld < b1 - b0)) return fail(GBD_EINVAL, "gbd_rect_hits: bad rectangle");
+    if (d_hits && !d_hit_count) return fail(GBD_EINVAL, "gbd_rect_hits: a hit list needs d_hit_count");
+    if ((d_ref_labels == nullptr) != (d_row_labels == nullptr))
+        return fail(GBD_EINVAL, "gbd_rect_hits: annotation needs both d_ref_labels and d_row_labels");
+    GBD_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (d_hit_count) GBD_CUDA_TRY(cudaMemsetAsync(d_hit_count, 0, sizeof(uint64_t), st));
+    if (d_row_labels && a1 > a0) GBD_CUDA_TRY(cudaMemsetAsync(d_row_labels, 0xff, (a1 - a0) * sizeof(int32_t), st));
+    if (a0 == a1 || b0 == b1) return GBD_OK;
+    return launch_rect_epilogue(d_rect, ld, A->view(), a0, a1, B->view(), b0, b1, Threshold{th->num, th->den, th->abs_max},
+                                d_hits, d_hits ? hit_capacity : 0, reinterpret_cast<unsigned long long *>(d_hit_count),
+                                d_ref_labels, d_row_labels, ctx->sm_count, st);
+}
+
 int gbd_tri_components(gbd_ctx *ctx, const gbd_set *set, const uint16_t *d_tri, const gbd_threshold *th,
                        uint32_t *d_labels, uint64_t *d_edges, void *stream)
 {

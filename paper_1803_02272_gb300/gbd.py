@@ -34,6 +34,7 @@ EXPORTS = [
     "gbd_server_wait", "gbd_server_destroy", "gbd_last_error", "gbd_probe_op_rate",
     "gbd_kernel_launches", "gbd_tile_noalloc", "gbd_sqdist_square", "gbd_gram_apply", "gbd_mds",
     "gbd_tile_hits", "gbd_threshold_components", "gbd_tri_components", "gbd_batch_tuning",
+    "gbd_rect_hits",
 ]
 
 
@@ -85,6 +86,8 @@ def _declare(lib):
         "gbd_tile_hits": ([vp, vp, u64, u64, vp, u64, u64, ctypes.POINTER(GbdThreshold), vp, u64, vp, u64,
                            vp, vp, vp, vp], ci),
         "gbd_threshold_components": ([vp, vp, ctypes.POINTER(GbdThreshold), vp, vp, vp, vp], ci),
+        "gbd_rect_hits": ([vp, vp, u64, u64, vp, u64, u64, vp, u64, ctypes.POINTER(GbdThreshold), vp, u64,
+                           vp, vp, vp, vp], ci),
         "gbd_tri_components": ([vp, vp, vp, ctypes.POINTER(GbdThreshold), vp, vp, vp], ci),
         "gbd_batch_tuning": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ci)], ci),
@@ -269,6 +272,15 @@ def gbd_tile_hits(ctx: int, A: int, a0: int, a1: int, B: int, b0: int, b1: int, 
                   d_ref_labels=None, d_row_labels=None, stream=None) -> None:
     """Rectangle with the threshold epilogue (hit list and/or row annotation)."""
     _check(_lib.gbd_tile_hits(ctx, A, a0, a1, B, b0, b1, ctypes.byref(th), _ptr(d_out), ld, _ptr(d_hits),
+                              hit_capacity, _ptr(d_hit_count), _ptr(d_ref_labels), _ptr(d_row_labels),
+                              _stream(stream)))
+
+
+def gbd_rect_hits(ctx: int, A: int, a0: int, a1: int, B: int, b0: int, b1: int, d_rect, ld: int,
+                  th: GbdThreshold, d_hits=None, hit_capacity: int = 0, d_hit_count=None, d_ref_labels=None,
+                  d_row_labels=None, stream=None) -> None:
+    """Threshold epilogue over an already computed rectangle."""
+    _check(_lib.gbd_rect_hits(ctx, A, a0, a1, B, b0, b1, _ptr(d_rect), ld, ctypes.byref(th), _ptr(d_hits),
                               hit_capacity, _ptr(d_hit_count), _ptr(d_ref_labels), _ptr(d_row_labels),
                               _stream(stream)))
 

@@ -197,3 +197,30 @@ def test_tri_components_from_oracle_triangle(env):
         e = oth.threshold_edges(tri, rs.lengths, num, den, abs_max)
         assert int(edges.cpu().numpy()[0]) == len(e)
         np.testing.assert_array_equal(labels.cpu().numpy().astype(np.int64), oth.components(rs.n, e))
+
+
+def test_rect_hits_over_oracle_rectangle(env, ref_and_queries):
+    """The epilogue alone over a rectangle the oracle computed (uploaded), two rules."""
+    gbd, torch = env
+    ref, ref_lab, qs, D = ref_and_queries
+    ctx = _ctx(gbd)
+    A, B = ctx.load(qs), ctx.load(ref)
+    a0, a1, b0, b1 = 3, 80, 10, 490
+    sub = np.ascontiguousarray(D[a0:a1, b0:b1])
+    ld = b1 - b0
+    d_rect = torch.from_numpy(sub.view(np.int16).ravel()).cuda()
+    cap = sub.size
+    hits = torch.empty(3 * cap, dtype=torch.int32, device="cuda")
+    count = torch.empty(1, dtype=torch.int64, device="cuda")
+    labs = torch.from_numpy(ref_lab).cuda()
+    rows = torch.empty(a1 - a0, dtype=torch.int32, device="cuda")
+    for num, den, abs_max in [(6, 100, 65535), (1, 1, 15)]:
+        gbd.gbd_rect_hits(ctx.handle, A.handle, a0, a1, B.handle, b0, b1, d_rect, ld,
+                          gbd.threshold(num, den, abs_max), hits, cap, count, labs, rows)
+        torch.cuda.synchronize()
+        n, got = _hits_of(torch, hits, count, cap)
+        want = {(a0 + i, b0 + j, d) for i, j, d in oth.hits_rect(sub, qs.lengths[a0:a1], ref.lengths[b0:b1],
+                                                                   num, den, abs_max)}
+        assert n == len(want) and got == want
+        ann = oth.annotate(sub, qs.lengths[a0:a1], ref.lengths[b0:b1], ref_lab[b0:b1], num, den, abs_max)
+        np.testing.assert_array_equal(rows.cpu().numpy(), ann)
