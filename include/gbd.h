@@ -165,8 +165,10 @@ typedef struct {
     uint32_t abs_max;
 } gbd_threshold;
 
-/* Rectangle with the threshold applied as each distance is computed (section 4.3:
- * sample reads against annotated reference reads).  Any of the outputs may be NULL:
+/* Rectangle with the threshold applied to every distance (section 4.3: sample reads
+ * against annotated reference reads): the distances are computed into d_out (or, if it is
+ * NULL, a scratch rectangle allocated and freed on `stream`), then one streaming pass
+ * applies the rule.  Any of the outputs may be NULL:
  *   d_out         the dense rectangle, as gbd_tile (ld >= b1-b0);
  *   d_hits        up to hit_capacity hits as 3 uint32 each: row read index (in A), column
  *                 read index (in B), d -- in no particular order; needs d_hit_count;
@@ -193,9 +195,11 @@ int gbd_rect_hits(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, cons
 /* Connected components of the threshold graph of a read set (section 5: vertices are the
  * reads, an edge joins i < j when the pair is a hit).  d_labels (device, n uint32):
  * the smallest read index of each read's component.  d_edges (device, one uint64, may be
- * NULL): the number of edges.  d_tri (may be NULL): the dense triangle as gbd_all_pairs,
- * computed in the same pass.  The unions happen as the distances are computed; no edge
- * list is stored.  Asynchronous on `stream`. */
+ * NULL): the number of edges.  d_tri (may be NULL): the dense triangle as gbd_all_pairs;
+ * when NULL a scratch triangle (n(n-1) bytes) is allocated and freed on `stream`.  After
+ * the distances, one streaming pass collects the edges (up to 64 Mi at a time, in 512 MB
+ * of scratch) and a lock-free union-find joins them; more edges fall back to direct
+ * unions over the triangle.  Asynchronous on `stream`. */
 int gbd_threshold_components(gbd_ctx *ctx, const gbd_set *set, const gbd_threshold *th, uint32_t *d_labels,
                              uint64_t *d_edges, uint16_t *d_tri, void *stream);
 
