@@ -143,3 +143,26 @@ def test_affine_server_rows_match_oracle(env):
     want = oracle.rect(q, 0, q.n, sub, 0, sub.n, gap_open=3)
     np.testing.assert_array_equal(got, want)
     srv.close()
+
+
+def test_full_reference_sampled():
+    """A request against the paper-scale resident reference (10^5 reads): sampled rows and
+    columns against the oracle."""
+    import torch
+    from paper_1803_02272_gb300 import gbd
+    ref_rs = synth.workload_paper_scale()
+    ctx = gbd.Context(0)
+    ref = ctx.load(ref_rs)
+    srv = gbd.Server(ctx, ref)
+    q = synth.workload_served_queries(1, 1.0, seed=1005, nq_hi=64)[0].reads
+    t, out = srv.submit(q)
+    srv.wait(t)
+    torch.cuda.synchronize()
+    got = gbd.as_uint16(out)
+    rng = np.random.default_rng(7)
+    rows = rng.integers(0, q.n, size=min(q.n, 4))
+    cols = rng.integers(0, ref_rs.n, size=500)
+    for r in rows:
+        want = oracle.pairs(q, np.full(len(cols), r), cols, ref_rs)
+        np.testing.assert_array_equal(got[r, cols], want)
+    srv.close()
