@@ -13,8 +13,8 @@
 //   orthonormalise        Gram S = Y^T Y (float64), Cholesky S = R^T R, Q = Y R^-1
 //                         (columns whose pivot falls below a floor dropped); once between
 //                         products, twice for the basis that B is formed on
-//   eigenpairs of B       B = Q^T (G Q) by the same Gram kernel, Jacobi (float32 with
-//                         float64 angles), eigenvalues sorted down, coordinates
+//   eigenpairs of B       B = Q^T (G Q) by the same Gram kernel, threshold Jacobi in
+//                         float32, eigenvalues sorted down, coordinates
 //                         Q V_r diag(max(lambda, 0)^1/2)
 // All reductions run in a fixed order, so results do not depend on scheduling.
 #include <cuda_fp16.h>
@@ -379,8 +379,8 @@ chol_inverse_kernel(const double *__restrict__ S_in, uint32_t k, double floor_re
 // ------------------------------------------------------------------ symmetric eigensolver
 // Eigenpairs of the small symmetric B = Q^T G Q: cyclic Jacobi with the round-robin
 // ordering (k/2 disjoint rotations per round, k-1 rounds per sweep), one block.  The
-// matrix and the rotations live in float32 (this part's output is float32, and float64
-// arithmetic is scarce on this GPU); each rotation angle is computed in float64.  A pair is
+// matrix, the rotations and their angles live in float32 (this part's output is float32,
+// and float64 arithmetic is scarce on this GPU).  A pair is
 // rotated only while its off-diagonal entry exceeds 1e-6 of the matrix norm (threshold
 // Jacobi); the sweeps stop when one makes no rotation.  Outputs: the r largest eigenvalues in order into lambda, and
 // T = V_r diag(max(lambda, 0)^1/2).  flags bit 0: no convergence; bit 1: non-finite input.
@@ -419,6 +419,7 @@ jacobi_kernel(const double *__restrict__ S_in, uint32_t k, uint32_t r, float *__
     }
     if (threadIdx.x == 0) fro = sqrt(red[0]);
     __syncthreads();
+    const float fro_floor = (float)(kJacobiTol * fro);
     const uint32_t half = k / 2;
     bool converged = false;
     for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
@@ -430,19 +431,22 @@ jacobi_kernel(const double *__restrict__ S_in, uint32_t k, uint32_t r, float *__
                 auto at = [&](uint32_t pos) -> uint32_t { return pos == 0 ? 0u : 1u + (pos - 1 + round) % (k - 1); };
                 uint32_t p = at(threadIdx.x), q = at(k - 1 - threadIdx.x);
                 if (p > q) { const uint32_t t = p; p = q; q = t; }
-                const double apq = A[p * k + q], app = A[p * k + p], aqq = A[q * k + q];
-                double c = 1.0, s = 0.0;
+                const float apq = A[p * k + q], app = A[p * k + p], aqq = A[q * k + q];
+                float c = 1.f, s = 0.f;
                 // negligible against the matrix norm (float32 cannot resolve less)
-                const double floor = kJacobiTol * fro;
-                if (fabs(apq) > floor) {
-                    const double theta = (aqq - app) / (2.0 * apq);
-                    const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                    c = 1.0 / sqrt(t * t + 1.0);
+                if (fabsf(apq) > fro_floor) {
+                    const float theta = (aqq - app) / (2.f * apq);
+                    // t = tan of the rotation angle, the root of smaller magnitude; for a
+                    // huge theta, t = 1 / (2 theta) without forming theta^2
+                    const float at = fabsf(theta);
+                    const float t = (theta >= 0.f ? 1.f : -1.f) /
+                                    (at + (at < 1e18f ? sqrtf(theta * theta + 1.f) : at));
+                    c = rsqrtf(t * t + 1.f);
                     s = t * c;
                     rotated = 1;
                 }
-                cs[threadIdx.x] = (float)c;
-                sn[threadIdx.x] = (float)s;
+                cs[threadIdx.x] = c;
+                sn[threadIdx.x] = s;
                 pp[threadIdx.x] = (int)p;
                 qq[threadIdx.x] = (int)q;
             }

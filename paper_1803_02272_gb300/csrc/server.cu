@@ -40,6 +40,7 @@ enum ReqState { REQ_QUEUED = 0, REQ_ACTIVE = 1, REQ_DONE = 2, REQ_FAILED = 3 };
 // 64 Mi pairs when much work is queued (fewer, larger batches keep the GPU saturated).
 constexpr uint64_t kChunkPairs = 12u << 20;
 constexpr uint64_t kMaxChunkPairs = 64u << 20;
+constexpr double kAgeSeconds = 1.0;    // waiting time that halves a request's sort key
 constexpr int kSlots = 2;                     // chunk batches in flight
 
 struct Request {
@@ -60,6 +61,7 @@ struct Request {
     cudaEvent_t packed = nullptr;
     uint64_t next_query = 0;         // first query not yet dispatched
     uint64_t chunks_inflight = 0;
+    std::chrono::steady_clock::time_point submitted;
 };
 
 struct Piece {
@@ -259,9 +261,17 @@ std::vector<Piece> next_pieces(gbd_server *srv)
     std::vector<Request *> cand;
     for (Request *r : srv->active)
         if (r->next_query < r->nq && r->error.empty()) cand.push_back(r);
-    std::sort(cand.begin(), cand.end(), [](const Request *a, const Request *b) {
-        return (a->nq - a->next_query) < (b->nq - b->next_query) ||
-               ((a->nq - a->next_query) == (b->nq - b->next_query) && a->ticket < b->ticket);
+    // Shortest remaining work first, aged: a request's remaining queries count as
+    // remaining / (1 + waited / kAgeSeconds), so a large request that has waited long
+    // enough is served before newer small ones instead of starving.
+    const auto now = std::chrono::steady_clock::now();
+    auto key = [&](const Request *r) {
+        const double waited = std::chrono::duration<double>(now - r->submitted).count();
+        return (double)(r->nq - r->next_query) / (1.0 + waited / kAgeSeconds);
+    };
+    std::sort(cand.begin(), cand.end(), [&](const Request *a, const Request *b) {
+        const double ka = key(a), kb = key(b);
+        return ka < kb || (ka == kb && a->ticket < b->ticket);
     });
     std::vector<Piece> out;
     const uint64_t n_ref = srv->ref->n;
@@ -416,6 +426,7 @@ int gbd_server_submit(gbd_server *srv, const uint8_t *seq, const uint64_t *offse
             return fail(GBD_EBUDGET, "gbd_server_submit: request needs " + std::to_string(r->footprint) +
                                          " bytes, above the server budget of " + std::to_string(srv->budget));
         r->ticket = srv->next_ticket++;
+        r->submitted = std::chrono::steady_clock::now();
         *ticket = r->ticket;
         srv->queue.push_back(r.get());
         srv->table.emplace(r->ticket, std::move(r));
