@@ -646,7 +646,8 @@ int gbd_rect_hits(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, cons
     if (rc != GBD_OK) return rc;
     if (a0 > a1 || a1 > A->n || b0 > b1 || b1 > B->n)
         return fail(GBD_EINVAL, "gbd_rect_hits: row or column range outside the sets");
-    if (a1 > a0 && b1 > b0 && (!d_rect || ld < b1 - b0)) return fail(GBD_EINVAL, "gbd_rect_hits: bad rectangle");
+    if (a1 > a0 && b1 > b0 && (!d_rect || ld < b1 - b0 || reinterpret_cast<uintptr_t>(d_rect) % 2 != 0))
+        return fail(GBD_EINVAL, "gbd_rect_hits: bad rectangle");
     if (d_hits && !d_hit_count) return fail(GBD_EINVAL, "gbd_rect_hits: a hit list needs d_hit_count");
     if ((d_ref_labels == nullptr) != (d_row_labels == nullptr))
         return fail(GBD_EINVAL, "gbd_rect_hits: annotation needs both d_ref_labels and d_row_labels");

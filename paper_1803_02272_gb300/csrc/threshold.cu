@@ -10,9 +10,9 @@
 //     union-find forest.  A root is only ever hooked under a smaller root, so every
 //     component ends with its smallest read as the root; a last pass points every read
 //     at its root.
-// Both kernels read each distance once (2 bytes; the triangle pass with 16-byte loads
-// over the flat triangle) plus the column read's length (cache-resident): they are
-// HBM-bound streams.
+// Both streams read each distance once with 16-byte loads and test it against a table of
+// per-read bounds (hit_bound, two entries per SIMD instruction), so they run at HBM speed
+// rather than at the speed of the integer test.
 #include "gbd_internal.cuh"
 
 namespace gbd {
@@ -22,14 +22,6 @@ __device__ __forceinline__ bool is_hit(uint32_t d, uint32_t la, uint32_t lb, con
 {
     const uint32_t L = la > lb ? la : lb;
     return d <= th.abs_max && (uint64_t)d * th.den <= (uint64_t)th.num * L;
-}
-
-// The same test in 32-bit arithmetic, exact when num and den are below 2^16 (d and the
-// lengths are below 2^16, so both products fit).
-__device__ __forceinline__ bool is_hit32(uint32_t d, uint32_t la, uint32_t lb, const Threshold &th)
-{
-    const uint32_t L = la > lb ? la : lb;
-    return d <= th.abs_max && d * th.den <= th.num * L;
 }
 
 __device__ __forceinline__ uint32_t uf_load(const uint32_t *p)
@@ -64,48 +56,181 @@ __device__ __forceinline__ void uf_union(uint32_t *parent, uint32_t a, uint32_t 
     }
 }
 
-// One block per row at a time (rows strided over the grid), threads along the row.
-__global__ void __launch_bounds__(256)
-rect_epilogue_kernel(const uint16_t *__restrict__ out, uint64_t ld, const uint16_t *__restrict__ lenA, uint64_t a0,
-                     uint64_t a1, const uint16_t *__restrict__ lenB, uint64_t b0, uint64_t b1, Threshold th,
-                     uint32_t *hits, uint64_t cap, unsigned long long *count, const int32_t *__restrict__ col_labels,
-                     int32_t *row_labels)
+// Largest distance that can be a hit when a read of length `len` is the longer of the
+// pair: min(abs_max, floor(num * len / den)), at most 65535.  It is non-decreasing in the
+// length, so the hit rule for reads of lengths la, lb is d <= max(bound(la), bound(lb)).
+__device__ __forceinline__ uint32_t hit_bound(uint32_t len, const Threshold &th)
 {
-    const uint64_t nb = b1 - b0;
-    for (uint64_t r = a0 + blockIdx.x; r < a1; r += gridDim.x) {
-        const uint32_t la = lenA[r];
-        const uint16_t *row = out + (r - a0) * ld;
-        int32_t mine = -1;                       // this thread's view of the row's species
-        for (uint64_t c = threadIdx.x; c < nb; c += blockDim.x) {
-            const uint32_t d = row[c];
-            const uint64_t col = b0 + c;
-            if (!is_hit(d, la, lenB[col], th)) continue;
-            if (count) {
-                const unsigned long long slot = atomicAdd(count, 1ull);
+    uint64_t q = (uint64_t)th.num * len / th.den;
+    if (q > th.abs_max) q = th.abs_max;
+    return q > 65535u ? 65535u : (uint32_t)q;
+}
+
+// T[j] = hit_bound(len[j]) for j < n, 0 for the padding up to n_pad.
+__global__ void hit_bound_kernel(const uint16_t *__restrict__ len, uint64_t n, uint64_t n_pad, Threshold th,
+                                 uint16_t *T)
+{
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_pad; j += (uint64_t)gridDim.x * blockDim.x)
+        T[j] = j < n ? (uint16_t)hit_bound(len[j], th) : (uint16_t)0;
+}
+
+// Hit mask of eight distances of one row (w: two per word, the first in the low half)
+// against the row's bound ti and the column bounds T[j .. j+7]: bit e set when entry e
+// is a hit.  Two entries per instruction: the column bounds arrive as packed pairs (a
+// 16-bit funnel shift when j is odd), the per-pair bound is a packed max and the test a
+// packed unsigned <=.  T must be 4-byte aligned with T[j + 9] readable.
+__device__ __forceinline__ uint32_t hits8(const uint32_t w[4], uint32_t ti, const uint16_t *__restrict__ T, uint64_t j)
+{
+    const uint32_t *Tw = reinterpret_cast<const uint32_t *>(T) + (j >> 1);
+    const uint32_t sh = (uint32_t)(j & 1) * 16u;
+    uint32_t W[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) W[k] = __ldg(Tw + k);
+    const uint32_t ti2 = ti * 0x10001u;
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t t = __funnelshift_r(W[k], W[k + 1], sh);
+        const uint32_t c = __vsetleu2(w[k], __vmaxu2(ti2, t));     // 1 in each half that is a hit
+        m |= ((c | (c >> 15)) & 3u) << (2 * k);
+    }
+    return m;
+}
+
+// Reserves `cnt` consecutive slots for each lane of a full warp with one atomic: returns
+// the lane's first slot.
+__device__ __forceinline__ unsigned long long warp_reserve(unsigned long long *count, uint32_t cnt)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total) base = atomicAdd(count, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + (incl - cnt);
+}
+
+// Row label lattice: -1 (no vote yet) is neutral, -2 (ambiguous) absorbs, two different
+// species give -2.
+__device__ __forceinline__ int32_t label_join(int32_t x, int32_t y)
+{
+    return x == -1 ? y : (y == -1 || y == x) ? x : -2;
+}
+
+// Joins v into *p.  Every successful exchange moves *p up the three-level lattice, so the
+// loop retries at most twice after a lost race.
+__device__ __forceinline__ void label_join_atomic(int32_t *p, int32_t v)
+{
+    if (v == -1) return;
+    int32_t old = *reinterpret_cast<volatile int32_t *>(p);
+    for (int it = 0; it < 4; ++it) {
+        const int32_t nv = label_join(old, v);
+        if (nv == old) return;
+        const int32_t prev = atomicCAS(p, old, nv);
+        if (prev == old) return;
+        old = prev;
+    }
+}
+
+constexpr uint32_t kRectSegVec = 1024;     // 8-entry vectors per rectangle work unit
+
+// The rectangle as (row, segment) work units strided over the grid: a row's entries from
+// its first 16-byte boundary on are read as 8-entry vectors, kRectSegVec vectors per
+// segment; segment 0 also takes the (fewer than 16) entries before the boundary and after
+// the last full vector.  Hits are appended with one atomic per warp; a unit's species
+// view is combined in the block, then joined into the row's label (pre-set to -1).
+// TB[c] = hit_bound of column b0 + c, padded past nb.
+__global__ void __launch_bounds__(256)
+rect_epilogue_kernel(const uint16_t *__restrict__ out, uint64_t ld, const uint16_t *__restrict__ lenA,
+                     uint64_t a0, uint64_t a1, const uint16_t *__restrict__ TB, uint64_t b0, uint64_t nb,
+                     Threshold th, uint32_t *hits, uint64_t cap, unsigned long long *count,
+                     const int32_t *__restrict__ col_labels, int32_t *row_labels)
+{
+    __shared__ int32_t lab[8];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t rows = a1 - a0;
+    const uint64_t nseg = ((nb + 7) / 8 + kRectSegVec - 1) / kRectSegVec;
+    for (uint64_t u = blockIdx.x; u < rows * nseg; u += gridDim.x) {
+        const uint64_t rr = u / nseg, seg = u - rr * nseg;
+        const uint64_t r = a0 + rr;
+        const uint32_t ti = hit_bound(lenA[r], th);
+        const uint16_t *row = out + rr * ld;
+        uint64_t head = ((16u - (uint32_t)(reinterpret_cast<uintptr_t>(row) & 15u)) & 15u) / 2u;
+        if (head > nb) head = nb;
+        const uint64_t nvec = (nb - head) / 8;
+        const uint64_t tail0 = head + 8 * nvec;
+        int32_t mine = -1;
+        // vectors of this segment; the loop bound is warp-uniform so all lanes vote
+        const uint64_t v0 = seg * kRectSegVec, v1 = min(nvec, v0 + kRectSegVec);
+        for (uint64_t vb = v0 + warp * 32; vb < v1; vb += blockDim.x) {
+            const uint64_t v = vb + lane;
+            uint32_t hm = 0, w[4] = {0u, 0u, 0u, 0u};
+            const uint64_t c = head + 8 * v;
+            if (v < v1) {
+                const uint4 x = __ldg(reinterpret_cast<const uint4 *>(row + c));
+                w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+                hm = hits8(w, ti, TB, c);
+            }
+            if (!__any_sync(0xffffffffu, hm != 0)) continue;
+            unsigned long long slot = count ? warp_reserve(count, __popc(hm)) : 0;
+            const uint64_t lo = (uint64_t)w[1] << 32 | w[0], hi = (uint64_t)w[3] << 32 | w[2];
+            while (hm) {
+                const int e = __ffs(hm) - 1;
+                hm &= hm - 1;
+                const uint32_t d = (uint32_t)(((e < 4) ? lo : hi) >> (16 * (e & 3))) & 0xffffu;
+                const uint64_t col = b0 + c + e;
                 if (hits && slot < cap) {
                     hits[3 * slot] = (uint32_t)r;
                     hits[3 * slot + 1] = (uint32_t)col;
                     hits[3 * slot + 2] = d;
                 }
+                ++slot;
+                if (row_labels) {
+                    const int32_t s = col_labels[col];
+                    if (s >= 0) mine = label_join(mine, s);
+                }
             }
-            if (row_labels) {
-                const int32_t s = col_labels[col];
-                if (s >= 0) mine = (mine == -1 || mine == s) ? s : -2;
+        }
+        // entries before the first boundary and after the last vector: warp 0 of segment 0
+        if (seg == 0 && warp == 0) {
+            const uint64_t ntail = nb - tail0;
+            uint32_t hit = 0, d = 0;
+            uint64_t c = 0;
+            if (lane < head + ntail) {
+                c = lane < head ? lane : tail0 + (lane - head);
+                d = row[c];
+                hit = d <= max(ti, (uint32_t)TB[c]);
+            }
+            if (__any_sync(0xffffffffu, hit)) {
+                const unsigned long long slot = count ? warp_reserve(count, hit) : 0;
+                if (hit) {
+                    if (hits && slot < cap) {
+                        hits[3 * slot] = (uint32_t)r;
+                        hits[3 * slot + 1] = (uint32_t)(b0 + c);
+                        hits[3 * slot + 2] = d;
+                    }
+                    if (row_labels) {
+                        const int32_t s = col_labels[b0 + c];
+                        if (s >= 0) mine = label_join(mine, s);
+                    }
+                }
             }
         }
         if (row_labels) {
-            // combine the threads' views: -1 is neutral, -2 absorbs, two species give -2
-            __shared__ int32_t lab[256];
-            lab[threadIdx.x] = mine;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mine = label_join(mine, __shfl_xor_sync(0xffffffffu, mine, o));
+            if (lane == 0) lab[warp] = mine;
             __syncthreads();
-            for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-                if ((int)threadIdx.x < w) {
-                    const int32_t x = lab[threadIdx.x], y = lab[threadIdx.x + w];
-                    lab[threadIdx.x] = (x == -1) ? y : (y == -1 || y == x) ? x : -2;
-                }
-                __syncthreads();
+            if (threadIdx.x == 0) {
+                int32_t x = -1;
+                for (uint32_t k = 0; k < blockDim.x / 32; ++k) x = label_join(x, lab[k]);
+                label_join_atomic(row_labels + rr, x);
             }
-            if (threadIdx.x == 0) row_labels[r - a0] = lab[0];
             __syncthreads();
         }
     }
@@ -168,16 +293,16 @@ __device__ __forceinline__ void tri_advance(uint64_t &i, uint64_t &j, uint64_t s
 
 // The triangle as one flat stream: each warp owns a contiguous run of 256-entry spans
 // and lane l reads entries 8l .. 8l+7 of a span with one 16-byte load (the triangle must
-// be 16-byte aligned).  Hits are appended to an edge list (one atomic per warp and entry
-// slot, ballot-aggregated): the unions run afterwards one edge per thread, so a warp
-// whose rows are full of hits does not serialise the latency of its unions.  Hits are
-// rare, so each lane first tests its eight entries into a bit mask and the warp takes the
-// append path only when some lane has one.  Every hit is counted; edges past the list's
-// capacity are left to tri_union_rows_kernel.
-template <bool NARROW>
+// be 16-byte aligned), the next span's load issued before the current span is tested.
+// A lane whose eight entries lie in one row tests them two at a time against the bound
+// table T (hits8); a lane across a row end or the triangle's end tests entry by entry.
+// Hits are appended to an edge list (one atomic per warp, only when some lane has a
+// hit): the unions run afterwards one edge per thread, so a warp whose rows are full of
+// hits does not serialise the latency of its unions.  Every hit is counted; edges past
+// the list's capacity are left to tri_union_rows_kernel.
 __global__ void __launch_bounds__(256)
-tri_hits_stream_kernel(const uint16_t *__restrict__ tri, const uint16_t *__restrict__ len, uint64_t n,
-                       uint64_t m, Threshold th, uint2 *edges, uint64_t cap, unsigned long long *count)
+tri_hits_stream_kernel(const uint16_t *__restrict__ tri, const uint16_t *__restrict__ T, uint64_t n,
+                       uint64_t m, uint2 *edges, uint64_t cap, unsigned long long *count)
 {
     const uint64_t warp_id = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -190,46 +315,38 @@ tri_hits_stream_kernel(const uint16_t *__restrict__ tri, const uint16_t *__restr
     const uint64_t k_first = s0 * 256 + 8 * lane;
     if (k_first < m) tri_unindex(k_first, n, i, j);
     const uint4 *t4 = reinterpret_cast<const uint4 *>(tri);
+    uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
+    if (k_first + 8 <= m) nxt = __ldg(t4 + k_first / 8);
     for (uint64_t sp = s0; sp < s1; ++sp) {
         const uint64_t kb = sp * 256 + 8 * lane;
-        uint32_t w[4] = {0u, 0u, 0u, 0u};
-        if (kb + 8 <= m) {
-            const uint4 v = __ldg(t4 + kb / 8);
-            w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
-        } else {
-            for (uint64_t e = 0; kb + e < m; ++e) w[e >> 1] |= (uint32_t)tri[kb + e] << (16 * (e & 1));
-        }
-        // bit e of hmask: entry e is a hit
-        uint32_t hmask = 0;
-        {
+        uint32_t w[4] = {nxt.x, nxt.y, nxt.z, nxt.w};
+        if (sp + 1 < s1 && kb + 256 + 8 <= m) nxt = __ldg(t4 + (kb + 256) / 8);
+        uint32_t hm = 0;
+        if (kb + 8 <= m && j + 7 < n) {
+            hm = hits8(w, T[i], T, j);
+        } else if (kb < m) {
+            if (kb + 8 > m) {                  // the triangle's last, partial vector
+                w[0] = w[1] = w[2] = w[3] = 0u;
+                for (uint64_t e = 0; kb + e < m; ++e) w[e >> 1] |= (uint32_t)tri[kb + e] << (16 * (e & 1));
+            }
             uint64_t ii = i, jj = j;
-            uint32_t lii = (kb < m) ? len[i] : 0u;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                if (kb + e < m) {
-                    const uint32_t d = (w[e >> 1] >> (16 * (e & 1))) & 0xffffu;
-                    const uint32_t lj = len[jj];
-                    if (NARROW ? is_hit32(d, lii, lj, th) : is_hit(d, lii, lj, th)) hmask |= 1u << e;
-                    if (++jj == n) { ++ii; jj = ii + 1; lii = len[ii < n ? ii : 0]; }
-                }
+            uint32_t ti = T[i];
+            for (int e = 0; e < 8 && kb + e < m; ++e) {
+                const uint32_t d = (w[e >> 1] >> (16 * (e & 1))) & 0xffffu;
+                if (d <= max(ti, (uint32_t)T[jj])) hm |= 1u << e;
+                if (++jj == n) { ++ii; jj = ii + 1; ti = T[ii]; }
             }
         }
-        if (__any_sync(0xffffffffu, hmask != 0)) {
+        if (__any_sync(0xffffffffu, hm != 0)) {
+            unsigned long long slot = warp_reserve(count, __popc(hm));
             uint64_t ii = i, jj = j;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const bool hit = (hmask >> e) & 1u;
-                const uint32_t mask = __ballot_sync(0xffffffffu, hit);
-                if (mask) {
-                    unsigned long long base = 0;
-                    if (lane == (uint32_t)(__ffs(mask) - 1)) base = atomicAdd(count, (unsigned long long)__popc(mask));
-                    base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
-                    if (hit) {
-                        const unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
-                        if (slot < cap) edges[slot] = make_uint2((uint32_t)ii, (uint32_t)jj);
-                    }
+            for (int e = 0; e < 8 && hm; ++e) {
+                if ((hm >> e) & 1u) {
+                    if (slot < cap) edges[slot] = make_uint2((uint32_t)ii, (uint32_t)jj);
+                    ++slot;
+                    hm &= ~(1u << e);
                 }
-                if (kb + e < m && ++jj == n) { ++ii; jj = ii + 1; }
+                if (++jj == n) { ++ii; jj = ii + 1; }
             }
         }
         tri_advance(i, j, 256, n);
@@ -310,9 +427,20 @@ int launch_rect_epilogue(const uint16_t *out, uint64_t ld, const DeviceReads &A,
 {
     if (a1 <= a0 || b1 <= b0) return GBD_OK;
     if (!count && !(row_labels && col_labels)) return GBD_OK;
-    rect_epilogue_kernel<<<grid_of(a1 - a0, sm_count, 8), 256, 0, st>>>(
-        out, ld, A.len, a0, a1, B.len, b0, b1, th, hits, cap, count, col_labels, row_labels && col_labels ? row_labels : nullptr);
-    return check_launch("rect_epilogue_kernel launch");
+    const uint64_t nb = b1 - b0, nb_pad = nb + 16;
+    uint16_t *TB = nullptr;
+    GBD_CUDA_TRY(cudaMallocAsync((void **)&TB, nb_pad * sizeof(uint16_t), st));
+    hit_bound_kernel<<<grid_of((nb_pad + 255) / 256, sm_count, 8), 256, 0, st>>>(B.len + b0, nb, nb_pad, th, TB);
+    int rc = check_launch("hit_bound_kernel launch");
+    if (rc == GBD_OK) {
+        const uint64_t nseg = ((nb + 7) / 8 + kRectSegVec - 1) / kRectSegVec;
+        rect_epilogue_kernel<<<grid_of((a1 - a0) * nseg, sm_count, 8), 256, 0, st>>>(
+            out, ld, A.len, a0, a1, TB, b0, nb, th, hits, cap, count, col_labels,
+            row_labels && col_labels ? row_labels : nullptr);
+        rc = check_launch("rect_epilogue_kernel launch");
+    }
+    cudaFreeAsync(TB, st);
+    return rc;
 }
 
 int launch_tri_components(const uint16_t *tri, const DeviceReads &S, const Threshold &th, uint32_t *parent,
@@ -333,12 +461,16 @@ int launch_tri_components(const uint16_t *tri, const DeviceReads &S, const Thres
             GBD_CUDA_TRY(cudaMallocAsync((void **)&edges, cap * sizeof(uint2), st));
             GBD_CUDA_TRY(cudaMallocAsync((void **)&cnt, sizeof(unsigned long long), st));
             GBD_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
-            const int grid = grid_of((m + 255) / 256, sm_count, 8);
-            if (th.num < 65536u && th.den < 65536u)
-                tri_hits_stream_kernel<true><<<grid, 256, 0, st>>>(tri, S.len, n, m, th, edges, cap, cnt);
-            else
-                tri_hits_stream_kernel<false><<<grid, 256, 0, st>>>(tri, S.len, n, m, th, edges, cap, cnt);
-            rc = check_launch("tri_hits_stream_kernel launch");
+            uint16_t *T = nullptr;
+            GBD_CUDA_TRY(cudaMallocAsync((void **)&T, (n + 16) * sizeof(uint16_t), st));
+            hit_bound_kernel<<<grid_of((n + 16 + 255) / 256, sm_count, 8), 256, 0, st>>>(S.len, n, n + 16, th, T);
+            rc = check_launch("hit_bound_kernel launch");
+            if (rc == GBD_OK) {
+                tri_hits_stream_kernel<<<grid_of((m + 255) / 256, sm_count, 8), 256, 0, st>>>(tri, T, n, m, edges, cap,
+                                                                                               cnt);
+                rc = check_launch("tri_hits_stream_kernel launch");
+            }
+            cudaFreeAsync(T, st);
             if (rc == GBD_OK) {
                 min_hook_kernel<<<grid_of((cap + 255) / 256, sm_count, 16), 256, 0, st>>>(edges, cap, cnt, parent);
                 rc = check_launch("min_hook_kernel launch");

@@ -224,3 +224,78 @@ def test_rect_hits_over_oracle_rectangle(env, ref_and_queries):
         assert n == len(want) and got == want
         ann = oth.annotate(sub, qs.lengths[a0:a1], ref.lengths[b0:b1], ref_lab[b0:b1], num, den, abs_max)
         np.testing.assert_array_equal(rows.cpu().numpy(), ann)
+
+
+def _lengths_set(st, n, lo, hi):
+    """Reads of random lengths in [lo, hi]; the epilogue reads only their lengths."""
+    L = st.integers(lo, hi, (n,))
+    return synth.from_strings(["A" * int(x) for x in L])
+
+
+def _near_rule(st, shape, la, lb, num, den, abs_max, p_near):
+    """Distances that sit on the decision boundary of the rule with probability p_near
+    (the largest hit value plus -1, 0 or +1), else just above it or far above it."""
+    L = np.maximum(la, lb).astype(np.int64)
+    edge = np.minimum(np.minimum(num * L // den, abs_max), 65535)
+    near = st.uniform(shape) < p_near
+    off = st.integers(-1, 1, shape)
+    above = edge + 1 + st.integers(0, 40, shape)
+    far = st.uniform(shape) < 0.5
+    d = np.where(near, edge + off, np.where(far, 65535, above))
+    return np.clip(d, 0, 65535).astype(np.uint16)
+
+
+@pytest.mark.parametrize("num,den,abs_max", [(7, 100, 65535), (1, 1, 25), (13, 50, 60)])
+def test_rect_hits_long_rows_every_alignment(env, num, den, abs_max):
+    """Rows longer than one work unit (20,003 columns), an odd row stride and a start two
+    bytes past an alignment boundary, so every row begins at a different offset within
+    16 bytes; distances on the rule's boundary.  Hit list and row labels exact."""
+    gbd, torch = env
+    st = synth.Stream(811, 0)
+    nq, nr = 24, 20003
+    qs, ref = _lengths_set(st, nq, 30, 700), _lengths_set(st, nr, 30, 700)
+    D = _near_rule(st, (nq, nr), qs.lengths[:, None], ref.lengths[None, :], num, den, abs_max, 6e-5)
+    ref_lab = st.integers(-1, 4, (nr,)).astype(np.int32)
+    ld = nr + 3
+    buf = np.full(1 + nq * ld, 7, np.uint16)
+    buf[1:].reshape(nq, ld)[:, :nr] = D
+    ctx = _ctx(gbd)
+    A, B = ctx.load(qs), ctx.load(ref)
+    d_buf = torch.from_numpy(buf.view(np.int16)).cuda()
+    cap = 4096
+    hits = torch.empty(3 * cap, dtype=torch.int32, device="cuda")
+    count = torch.empty(1, dtype=torch.int64, device="cuda")
+    rows = torch.empty(nq, dtype=torch.int32, device="cuda")
+    gbd.gbd_rect_hits(ctx.handle, A.handle, 0, nq, B.handle, 0, nr, d_buf[1:], ld, gbd.threshold(num, den, abs_max),
+                      hits, cap, count, torch.from_numpy(ref_lab).cuda(), rows)
+    torch.cuda.synchronize()
+    n, got = _hits_of(torch, hits, count, cap)
+    want = oth.hits_rect(D, qs.lengths, ref.lengths, num, den, abs_max)
+    assert 0 < len(want) < cap
+    assert n == len(want) and got == want
+    ann = oth.annotate(D, qs.lengths, ref.lengths, ref_lab, num, den, abs_max)
+    np.testing.assert_array_equal(rows.cpu().numpy(), ann)
+
+
+@pytest.mark.parametrize("num,den,abs_max", [(3, 100, 65535), (1, 1, 9)])
+def test_tri_components_synthetic_triangle(env, num, den, abs_max):
+    """A 3,001-read triangle of distances on the rule's boundary (random lengths): long
+    rows, row ends inside a lane's eight entries, a partial last vector."""
+    gbd, torch = env
+    st = synth.Stream(812, 0)
+    n = 3001
+    rs = _lengths_set(st, n, 20, 900)
+    iu, ju = np.triu_indices(n, 1)
+    L = rs.lengths
+    tri = _near_rule(st, (len(iu),), L[iu], L[ju], num, den, abs_max, 2e-4)
+    ctx = _ctx(gbd)
+    s = ctx.load(rs)
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    edges = torch.empty(1, dtype=torch.int64, device="cuda")
+    gbd.gbd_tri_components(ctx.handle, s.handle, torch.from_numpy(tri.view(np.int16)).cuda(),
+                           gbd.threshold(num, den, abs_max), labels, edges)
+    torch.cuda.synchronize()
+    e = oth.threshold_edges(tri, L, num, den, abs_max)
+    assert len(e) > 100
+    assert int(edges.cpu().numpy()[0]) == len(e)
+    np.testing.assert_array_equal(labels.cpu().numpy().astype(np.int64), oth.components(n, e))
