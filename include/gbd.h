@@ -70,12 +70,18 @@ typedef struct {
     uint64_t hbm_budget;  /* server admission budget in bytes; 0 = 90 % of free memory */
     uint32_t timeout_us;  /* bound on any host wait inside the library; 0 = 60 s */
     int16_t  gap_open;    /* affine gaps (Gotoh): a run of L gapped bases costs
-                             gap_open + L * gap; 0 = linear (default).  > 0 runs on the
-                             general kernel. */
+                             gap_open + L * gap; 0 = linear (default).  With match +1,
+                             mismatch -1, gap 1 and gap_open <= 1000 it runs on the
+                             systolic kernel, otherwise on the general kernel. */
+    uint64_t band_entries;/* scratch (uint16 entries) of gbd_threshold_components when it
+                             holds no triangle; 0 = 2^28 (512 MB) */
 } gbd_params;
 
 /* Fills *p with the defaults above. */
 void gbd_default_params(gbd_params *p);
+
+/* sizeof(gbd_params) as compiled into the library (for bindings that mirror the struct). */
+uint64_t gbd_params_size(void);
 
 /* Creates a context on CUDA device `device` (made current on the calling thread).
  * p == NULL selects the defaults.  EINVAL on a negative gap or bad enum values. */
@@ -195,11 +201,14 @@ int gbd_rect_hits(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, cons
 /* Connected components of the threshold graph of a read set (section 5: vertices are the
  * reads, an edge joins i < j when the pair is a hit).  d_labels (device, n uint32):
  * the smallest read index of each read's component.  d_edges (device, one uint64, may be
- * NULL): the number of edges.  d_tri (may be NULL): the dense triangle as gbd_all_pairs;
- * when NULL a scratch triangle (n(n-1) bytes) is allocated and freed on `stream`.  After
- * the distances, one streaming pass collects the edges (up to 64 Mi at a time, in 512 MB
- * of scratch) and a lock-free union-find joins them; more edges fall back to direct
- * unions over the triangle.  Asynchronous on `stream`. */
+ * NULL): the number of edges.  d_tri (may be NULL): when set, the dense triangle as
+ * gbd_all_pairs is computed into it and kept, then one streaming pass collects the
+ * edges (up to 64 Mi at a time, in 512 MB of scratch) and a lock-free union-find joins
+ * them, with direct unions over the triangle for any edges past 64 Mi.  When NULL the
+ * triangle is never held: bands of rows are computed in turn into a scratch rectangle
+ * of params.band_entries entries (default 512 MB) and each band's hits are joined into the forest before the next band
+ * (section 5's graph without the n(n-1)/2 distances in memory).  Asynchronous on
+ * `stream`; the scratch is allocated and freed on it. */
 int gbd_threshold_components(gbd_ctx *ctx, const gbd_set *set, const gbd_threshold *th, uint32_t *d_labels,
                              uint64_t *d_edges, uint16_t *d_tri, void *stream);
 

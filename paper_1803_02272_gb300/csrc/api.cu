@@ -208,6 +208,68 @@ static int tile_impl(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, c
     return rc;
 }
 
+// Distances of the rows [a0, a1) of a set against the reads after each row: row r's
+// pairs (r, j), j > r, go to out[(r - a0) * ld + (j - a0 - 1)] (the entries before
+// column r + 1 - a0 - 1 of each row are not written, or hold pairs with j <= r).
+static int band_impl(gbd_ctx *ctx, const gbd_set *set, uint64_t a0, uint64_t a1, uint16_t *out, uint64_t ld,
+                     cudaStream_t st)
+{
+    const uint64_t n = set->n;
+    if (a1 <= a0 || a0 + 1 >= n) return GBD_OK;
+    if (!use_systolic(ctx)) {
+        GeneralJob job{set->view(), set->view(), a0, a1, a0 + 1, n, ld, OUT_RECT, out};
+        return run_general(job, scoring_of(ctx), ctx->sm_count, st);
+    }
+    std::vector<SysEntry> entries;
+    std::vector<uint8_t> rows;
+    std::vector<uint32_t> long_rows;
+    for (uint64_t r = a0; r < a1 && r + 1 < n; ++r) {
+        if (set->h_len[r] <= kSystolicMaxQuery) {
+            entries.push_back({0u, (uint32_t)r, (uint32_t)(r + 1), (uint32_t)(n - r - 1)});
+            rows.push_back((uint8_t)systolic_rows(set->h_len[r]));
+        } else {
+            long_rows.push_back((uint32_t)r);
+        }
+    }
+    int rc = GBD_OK;
+    if (!entries.empty()) {
+        SysJob job{};
+        job.Q = job.S = set->view();
+        job.sub_perm = nullptr;
+        job.out = out;
+        job.ld = ld;
+        job.row0 = a0;
+        job.col0 = a0 + 1;
+        job.mode = OUT_RECT;
+        job.conversion = ctx->params.conversion;
+        job.gap_open = ctx->params.gap_open;
+        SysJob *d_job = nullptr;
+        SysPlan plan;
+        if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
+        if ((rc = build_plan(entries, rows, plan, false, st, 0, set->mean_len, ctx->sm_count)) != GBD_OK)
+            return rc;
+        rc = run_systolic(d_job, plan, ctx->sm_count, st, ctx->aux, ctx->fork, ctx->join, job.gap_open > 0);
+        cudaFreeAsync(d_job, st);
+        free_plan(plan, st);
+        if (rc != GBD_OK) return rc;
+    }
+    if (!long_rows.empty()) {
+        // whole rows of the rectangle [a0, a1) x [a0 + 1, n): the pairs with j <= r land in
+        // the row's unused entries
+        uint32_t *d_rows = nullptr;
+        if ((rc = upload(long_rows.data(), long_rows.size(), &d_rows, st)) != GBD_OK) return rc;
+        GeneralJob gj{set->view(), set->view(), a0, a1, a0 + 1, n, ld, OUT_RECT, out};
+        gj.rows = d_rows;
+        gj.nrows = long_rows.size();
+        rc = run_general(gj, scoring_of(ctx), ctx->sm_count, st);
+        cudaFreeAsync(d_rows, st);
+    }
+    return rc;
+}
+
+// Default entries of the band scratch of gbd_threshold_components without a triangle (512 MB).
+constexpr uint64_t kBandEntries = 1ull << 28;
+
 static int check_threshold(const gbd_threshold *th)
 {
     if (!th) return fail(GBD_EINVAL, "NULL threshold");
@@ -274,7 +336,6 @@ static int record_batch_graph(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const
 static int capture_batch(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const *samples, uint64_t ns,
                          uint16_t *const *d_tris)
 {
-    cudaStream_t cap = ctx->capture;
     std::vector<SysJob> jobs(ns);
     std::vector<SysEntry> entries;
     std::vector<uint8_t> rows;
@@ -376,6 +437,8 @@ void gbd_default_params(gbd_params *p)
     p->hbm_budget = 0;
     p->timeout_us = 0;
 }
+
+uint64_t gbd_params_size(void) { return sizeof(gbd_params); }
 
 int gbd_create(gbd_ctx **out, int device, const gbd_params *p)
 {
@@ -626,14 +689,33 @@ int gbd_threshold_components(gbd_ctx *ctx, const gbd_set *set, const gbd_thresho
     if (d_edges) GBD_CUDA_TRY(cudaMemsetAsync(d_edges, 0, sizeof(uint64_t), st));
     if (n == 0) return GBD_OK;
     const uint64_t m = n * (n - 1) / 2;
-    uint16_t *tri = d_tri;
-    if (!tri && m > 0) GBD_CUDA_TRY(cudaMallocAsync((void **)&tri, m * sizeof(uint16_t), st));
-    if (m > 0) rc = all_pairs_impl(ctx, set, tri, st);
-    if (rc == GBD_OK)
-        rc = launch_tri_components(tri, set->view(), Threshold{th->num, th->den, th->abs_max}, d_labels,
-                                   reinterpret_cast<unsigned long long *>(d_edges), ctx->sm_count, st);
-    if (!d_tri && tri) cudaFreeAsync(tri, st);
-    return rc;
+    const Threshold t{th->num, th->den, th->abs_max};
+    if (d_tri) {
+        // the whole triangle, kept for the caller, then one stream over it
+        if (m > 0) rc = all_pairs_impl(ctx, set, d_tri, st);
+        if (rc == GBD_OK)
+            rc = launch_tri_components(d_tri, set->view(), t, d_labels, reinterpret_cast<unsigned long long *>(d_edges),
+                                       ctx->sm_count, st);
+        return rc;
+    }
+    // bands of rows whose distances fit a bounded scratch: each band is computed, its hits
+    // joined into the forest, and the scratch reused
+    const uint64_t budget = ctx->params.band_entries ? ctx->params.band_entries : kBandEntries;
+    const uint64_t scratch = std::max<uint64_t>(1, std::min<uint64_t>(budget, n * (n - 1)));
+    uint16_t *rect = nullptr;
+    BandForest bf;
+    if (m > 0) GBD_CUDA_TRY(cudaMallocAsync((void **)&rect, scratch * sizeof(uint16_t), st));
+    rc = band_forest_begin(bf, set->view(), t, d_labels, scratch, ctx->sm_count, st);
+    for (uint64_t a0 = 0; rc == GBD_OK && a0 + 1 < n;) {
+        const uint64_t ld = n - a0 - 1;              // columns a0 + 1 .. n - 1
+        const uint64_t a1 = std::min<uint64_t>(n - 1, a0 + std::max<uint64_t>(1, scratch / ld));
+        rc = band_impl(ctx, set, a0, a1, rect, ld, st);
+        if (rc == GBD_OK) rc = band_forest_add(bf, rect, ld, set->view(), a0, a1, t, d_labels, ctx->sm_count, st);
+        a0 = a1;
+    }
+    const int erc = band_forest_end(bf, d_labels, n, reinterpret_cast<unsigned long long *>(d_edges), ctx->sm_count, st);
+    if (rect) cudaFreeAsync(rect, st);
+    return rc != GBD_OK ? rc : erc;
 }
 
 int gbd_rect_hits(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd_set *B, uint64_t b0,

@@ -153,6 +153,26 @@ int launch_rect_epilogue(const uint16_t *out, uint64_t ld, const DeviceReads &A,
 int launch_tri_components(const uint16_t *tri, const DeviceReads &S, const Threshold &th, uint32_t *parent,
                           unsigned long long *count, int sm_count, cudaStream_t st);
 
+// Threshold-graph components without the whole triangle: the caller computes the
+// distances of one band of rows [a0, a1) at a time into a rectangle whose row a0 + rr
+// holds columns j = a0 + 1 + c at rect[rr * ld + c] for c >= rr (that is, j > a0 + rr),
+// and hands each band to band_forest_add, which joins its hits into the forest `parent`.
+// begin sets every read to its own root; end points every read at its component's
+// smallest read, writes the number of hits to *count (if set) and frees the scratch.
+struct BandForest {
+    uint16_t *T = nullptr;                  // hit bound per read (n + 16 entries)
+    uint2 *edges = nullptr;                 // one band's hits
+    unsigned long long *cnt = nullptr;      // [0] hits of the band, [1] running total
+    uint64_t cap = 0;
+    bool first = true;                      // the forest is still fresh
+};
+int band_forest_begin(BandForest &bf, const DeviceReads &S, const Threshold &th, uint32_t *parent, uint64_t max_entries,
+                      int sm_count, cudaStream_t st);
+int band_forest_add(BandForest &bf, const uint16_t *rect, uint64_t ld, const DeviceReads &S, uint64_t a0, uint64_t a1,
+                    const Threshold &th, uint32_t *parent, int sm_count, cudaStream_t st);
+int band_forest_end(BandForest &bf, uint32_t *parent, uint64_t n, unsigned long long *count, int sm_count,
+                    cudaStream_t st);
+
 // Frees the context's cached batch graph.
 void free_batch_cache(gbd_ctx *ctx);
 

@@ -61,7 +61,8 @@ __device__ __forceinline__ void uf_union(uint32_t *parent, uint32_t a, uint32_t 
 // length, so the hit rule for reads of lengths la, lb is d <= max(bound(la), bound(lb)).
 __device__ __forceinline__ uint32_t hit_bound(uint32_t len, const Threshold &th)
 {
-    uint64_t q = (uint64_t)th.num * len / th.den;
+    uint64_t q = th.num <= 0xffffu ? (uint64_t)((th.num * len) / th.den)   // len < 2^16: fits 32 bits
+                                   : (uint64_t)th.num * len / th.den;
     if (q > th.abs_max) q = th.abs_max;
     return q > 65535u ? 65535u : (uint32_t)q;
 }
@@ -95,6 +96,29 @@ __device__ __forceinline__ uint32_t hits8(const uint32_t w[4], uint32_t ti, cons
         m |= ((c | (c >> 15)) & 3u) << (2 * k);
     }
     return m;
+}
+
+// Whether any of the eight entries of hits8 is a hit, at six instructions per two
+// entries: where an entry is a hit its packed minimum with the bound equals the entry,
+// so (min ^ d) has a zero half there, and (x - 0x00010001) & ~x sets bit 15 of some half
+// exactly when x has a zero half (a borrow out of a zero low half can only add a flag
+// to the high half, never remove one).
+__device__ __forceinline__ bool any_hit8(const uint32_t w[4], uint32_t ti, const uint16_t *__restrict__ T, uint64_t j)
+{
+    const uint32_t *Tw = reinterpret_cast<const uint32_t *>(T) + (j >> 1);
+    const uint32_t sh = (uint32_t)(j & 1) * 16u;
+    uint32_t W[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) W[k] = __ldg(Tw + k);
+    const uint32_t ti2 = ti * 0x10001u;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t t = __funnelshift_r(W[k], W[k + 1], sh);
+        const uint32_t x = __vminu2(w[k], __vmaxu2(ti2, t)) ^ w[k];
+        acc |= (x - 0x00010001u) & ~x;
+    }
+    return (acc & 0x80008000u) != 0;
 }
 
 // Reserves `cnt` consecutive slots for each lane of a full warp with one atomic: returns
@@ -137,103 +161,171 @@ __device__ __forceinline__ void label_join_atomic(int32_t *p, int32_t v)
     }
 }
 
-constexpr uint32_t kRectSegVec = 1024;     // 8-entry vectors per rectangle work unit
+constexpr uint32_t kRectSegVec = 4096;     // 8-entry vectors per rectangle work unit
 
-// The rectangle as (row, segment) work units strided over the grid: a row's entries from
-// its first 16-byte boundary on are read as 8-entry vectors, kRectSegVec vectors per
-// segment; segment 0 also takes the (fewer than 16) entries before the boundary and after
-// the last full vector.  Hits are appended with one atomic per warp; a unit's species
-// view is combined in the block, then joined into the row's label (pre-set to -1).
-// TB[c] = hit_bound of column b0 + c, padded past nb.
+// Where a rectangle's hits go and how its rows are laid out.
+struct RectOut {
+    uint32_t *hits;                 // (row, col, d) triples, or
+    uint2 *edges;                   // (row, col) pairs (when set)
+    uint64_t cap;
+    unsigned long long *count;      // every hit counted, also past cap
+    const int32_t *col_labels;      // species of column b0 + c (annotation), with
+    int32_t *row_labels;            // the label of row a0 + rr (pre-set to -1)
+};
+
+// Bookkeeping of one row of a rectangle: entries of row rr start at out + rr*ld + c_lo
+// (c_lo = rr for a triangle band, whose row a0 + rr holds columns b0 + rr ..).  Vectors
+// of 8 entries run from the row's first 16-byte boundary; head entries come before it,
+// tail entries after the last full vector.
+struct RowSpan {
+    const uint16_t *p;
+    uint64_t c_lo, head, nvec, tail0, nbr;
+};
+
+__device__ __forceinline__ RowSpan row_span(const uint16_t *out, uint64_t ld, uint64_t rr, uint64_t nb, bool band)
+{
+    RowSpan rs;
+    rs.c_lo = band ? rr : 0;
+    rs.nbr = nb > rs.c_lo ? nb - rs.c_lo : 0;
+    rs.p = out + rr * ld + rs.c_lo;
+    uint64_t head = ((16u - (uint32_t)(reinterpret_cast<uintptr_t>(rs.p) & 15u)) & 15u) / 2u;
+    rs.head = head > rs.nbr ? rs.nbr : head;
+    rs.nvec = (rs.nbr - rs.head) / 8;
+    rs.tail0 = rs.head + 8 * rs.nvec;
+    return rs;
+}
+
+// Records one hit at `slot` (already reserved).
+__device__ __forceinline__ void put_hit(const RectOut &o, unsigned long long slot, uint32_t r, uint32_t col, uint32_t d)
+{
+    if (slot >= o.cap) return;
+    if (o.edges) {
+        o.edges[slot] = make_uint2(r, col);
+    } else if (o.hits) {
+        o.hits[3 * slot] = r;
+        o.hits[3 * slot + 1] = col;
+        o.hits[3 * slot + 2] = d;
+    }
+}
+
+// The rectangle as (row, segment) work units strided over the grid, kRectSegVec vectors
+// of a row per segment; segment 0 also takes the row's (fewer than 16) head and tail
+// entries with one warp.  Hits are appended with one atomic per warp; a unit's species
+// view is combined in the block, then joined into the row's label.  Column bounds:
+// TB[toff + c] = hit_bound of column b0 + c (TB 4-byte aligned, toff 0 or 1, readable
+// 10 entries past the last column).
 __global__ void __launch_bounds__(256)
-rect_epilogue_kernel(const uint16_t *__restrict__ out, uint64_t ld, const uint16_t *__restrict__ lenA,
-                     uint64_t a0, uint64_t a1, const uint16_t *__restrict__ TB, uint64_t b0, uint64_t nb,
-                     Threshold th, uint32_t *hits, uint64_t cap, unsigned long long *count,
-                     const int32_t *__restrict__ col_labels, int32_t *row_labels)
+rect_epilogue_kernel(const uint16_t *__restrict__ out, uint64_t ld, bool band, const uint16_t *__restrict__ lenA,
+                     uint64_t a0, uint64_t a1, const uint16_t *__restrict__ TB, uint32_t toff, uint64_t b0,
+                     uint64_t nb, Threshold th, RectOut o)
 {
     __shared__ int32_t lab[8];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t rows = a1 - a0;
-    const uint64_t nseg = ((nb + 7) / 8 + kRectSegVec - 1) / kRectSegVec;
-    for (uint64_t u = blockIdx.x; u < rows * nseg; u += gridDim.x) {
-        const uint64_t rr = u / nseg, seg = u - rr * nseg;
+    const uint32_t rows = (uint32_t)(a1 - a0);                  // rows * nseg < 2^32 (host)
+    const uint32_t nseg = (uint32_t)(((nb + 7) / 8 + kRectSegVec - 1) / kRectSegVec);
+    const bool want_hits = o.count != nullptr;
+    const bool want_labels = o.row_labels != nullptr;
+    for (uint32_t u = blockIdx.x; u < rows * nseg; u += gridDim.x) {
+        const uint32_t rr = u / nseg, seg = u - rr * nseg;
         const uint64_t r = a0 + rr;
         const uint32_t ti = hit_bound(lenA[r], th);
-        const uint16_t *row = out + rr * ld;
-        uint64_t head = ((16u - (uint32_t)(reinterpret_cast<uintptr_t>(row) & 15u)) & 15u) / 2u;
-        if (head > nb) head = nb;
-        const uint64_t nvec = (nb - head) / 8;
-        const uint64_t tail0 = head + 8 * nvec;
+        const RowSpan rs = row_span(out, ld, rr, nb, band);
+        const uint64_t cb = b0 + rs.c_lo;            // column of the row's entry 0
+        const uint64_t tb = toff + rs.c_lo;          // its index in TB
         int32_t mine = -1;
         // vectors of this segment; the loop bound is warp-uniform so all lanes vote
-        const uint64_t v0 = seg * kRectSegVec, v1 = min(nvec, v0 + kRectSegVec);
-        for (uint64_t vb = v0 + warp * 32; vb < v1; vb += blockDim.x) {
-            const uint64_t v = vb + lane;
-            uint32_t hm = 0, w[4] = {0u, 0u, 0u, 0u};
-            const uint64_t c = head + 8 * v;
+        const uint32_t v0 = seg * kRectSegVec, v1 = (uint32_t)min(rs.nvec, (uint64_t)v0 + kRectSegVec);
+        const uint4 *pv = reinterpret_cast<const uint4 *>(rs.p + rs.head);
+        // TB from an even index at or before the bound of the row's vector 0 (so 32-bit
+        // loads stay aligned), and that bound's offset from there
+        const uint64_t t0 = tb + rs.head;
+        const uint16_t *tbv = TB + (t0 & ~1ull);
+        const uint32_t par = (uint32_t)(t0 & 1);
+        for (uint32_t vb = v0 + warp * 32; vb < v1; vb += blockDim.x) {
+            const uint32_t v = vb + lane;
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            bool cand = false;
             if (v < v1) {
-                const uint4 x = __ldg(reinterpret_cast<const uint4 *>(row + c));
+                const uint4 x = __ldg(pv + v);
                 w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
-                hm = hits8(w, ti, TB, c);
+                cand = any_hit8(w, ti, tbv, 8 * v + par);
             }
-            if (!__any_sync(0xffffffffu, hm != 0)) continue;
-            unsigned long long slot = count ? warp_reserve(count, __popc(hm)) : 0;
+            if (!__any_sync(0xffffffffu, cand)) continue;
+            const uint64_t c = rs.head + 8 * (uint64_t)v;
+            uint32_t hm = cand ? hits8(w, ti, TB, tb + c) : 0u;
+            unsigned long long slot = want_hits ? warp_reserve(o.count, __popc(hm)) : 0;
             const uint64_t lo = (uint64_t)w[1] << 32 | w[0], hi = (uint64_t)w[3] << 32 | w[2];
             while (hm) {
                 const int e = __ffs(hm) - 1;
                 hm &= hm - 1;
                 const uint32_t d = (uint32_t)(((e < 4) ? lo : hi) >> (16 * (e & 3))) & 0xffffu;
-                const uint64_t col = b0 + c + e;
-                if (hits && slot < cap) {
-                    hits[3 * slot] = (uint32_t)r;
-                    hits[3 * slot + 1] = (uint32_t)col;
-                    hits[3 * slot + 2] = d;
-                }
-                ++slot;
-                if (row_labels) {
-                    const int32_t s = col_labels[col];
-                    if (s >= 0) mine = label_join(mine, s);
+                const uint64_t col = cb + c + e;
+                if (want_hits) put_hit(o, slot++, (uint32_t)r, (uint32_t)col, d);
+                if (want_labels) {
+                    const int32_t sp = o.col_labels[col];
+                    if (sp >= 0) mine = label_join(mine, sp);
                 }
             }
         }
         // entries before the first boundary and after the last vector: warp 0 of segment 0
         if (seg == 0 && warp == 0) {
-            const uint64_t ntail = nb - tail0;
+            const uint64_t ntail = rs.nbr - rs.tail0;
             uint32_t hit = 0, d = 0;
             uint64_t c = 0;
-            if (lane < head + ntail) {
-                c = lane < head ? lane : tail0 + (lane - head);
-                d = row[c];
-                hit = d <= max(ti, (uint32_t)TB[c]);
+            if (lane < rs.head + ntail) {
+                c = lane < rs.head ? lane : rs.tail0 + (lane - rs.head);
+                d = rs.p[c];
+                hit = d <= max(ti, (uint32_t)TB[tb + c]);
             }
             if (__any_sync(0xffffffffu, hit)) {
-                const unsigned long long slot = count ? warp_reserve(count, hit) : 0;
+                const unsigned long long slot = want_hits ? warp_reserve(o.count, hit) : 0;
                 if (hit) {
-                    if (hits && slot < cap) {
-                        hits[3 * slot] = (uint32_t)r;
-                        hits[3 * slot + 1] = (uint32_t)(b0 + c);
-                        hits[3 * slot + 2] = d;
-                    }
-                    if (row_labels) {
-                        const int32_t s = col_labels[b0 + c];
-                        if (s >= 0) mine = label_join(mine, s);
+                    if (want_hits) put_hit(o, slot, (uint32_t)r, (uint32_t)(cb + c), d);
+                    if (want_labels) {
+                        const int32_t sp = o.col_labels[cb + c];
+                        if (sp >= 0) mine = label_join(mine, sp);
                     }
                 }
             }
         }
-        if (row_labels) {
+        if (want_labels) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mine = label_join(mine, __shfl_xor_sync(0xffffffffu, mine, o));
+            for (int k = 16; k > 0; k >>= 1) mine = label_join(mine, __shfl_xor_sync(0xffffffffu, mine, k));
             if (lane == 0) lab[warp] = mine;
             __syncthreads();
             if (threadIdx.x == 0) {
                 int32_t x = -1;
                 for (uint32_t k = 0; k < blockDim.x / 32; ++k) x = label_join(x, lab[k]);
-                label_join_atomic(row_labels + rr, x);
+                label_join_atomic(o.row_labels + rr, x);
             }
             __syncthreads();
         }
     }
+}
+
+// Direct unions over a triangle band (layout as in rect_epilogue_kernel with band set),
+// one block per row; runs only when the band's edge list overflowed (*count > cap).
+__global__ void __launch_bounds__(256)
+band_union_rows_kernel(const uint16_t *__restrict__ out, uint64_t ld, const uint16_t *__restrict__ T,
+                       uint64_t a0, uint64_t a1, uint64_t b0, uint64_t nb, uint32_t *parent,
+                       const unsigned long long *count, uint64_t cap)
+{
+    if (*count <= cap) return;
+    for (uint64_t rr = blockIdx.x; rr < a1 - a0; rr += gridDim.x) {
+        const uint64_t r = a0 + rr;
+        const uint32_t ti = T[r];
+        for (uint64_t c = rr + threadIdx.x; c < nb; c += blockDim.x) {
+            const uint64_t col = b0 + c;
+            if (out[rr * ld + c] <= max(ti, (uint32_t)T[col])) uf_union(parent, (uint32_t)r, (uint32_t)col);
+        }
+    }
+}
+
+// total += *count; *count = 0 (one thread).
+__global__ void band_total_kernel(unsigned long long *count, unsigned long long *total)
+{
+    *total += *count;
+    *count = 0;
 }
 
 __global__ void iota_kernel(uint32_t *a, uint64_t n)
@@ -280,28 +372,19 @@ __device__ __forceinline__ void tri_unindex(uint64_t k, uint64_t n, uint64_t &i,
     j = k - tri_row_start(i, n) + i + 1;
 }
 
-// Moves (i, j) forward by `steps` entries of the triangle.
-__device__ __forceinline__ void tri_advance(uint64_t &i, uint64_t &j, uint64_t steps, uint64_t n)
-{
-    j += steps;
-    while (j >= n && i + 2 < n) {
-        const uint64_t over = j - n;           // entries past the end of row i
-        ++i;
-        j = i + 1 + over;
-    }
-}
-
 // The triangle as one flat stream: each warp owns a contiguous run of 256-entry spans
 // and lane l reads entries 8l .. 8l+7 of a span with one 16-byte load (the triangle must
 // be 16-byte aligned), the next span's load issued before the current span is tested.
-// A lane whose eight entries lie in one row tests them two at a time against the bound
-// table T (hits8); a lane across a row end or the triangle's end tests entry by entry.
-// Hits are appended to an edge list (one atomic per warp, only when some lane has a
-// hit): the unions run afterwards one edge per thread, so a warp whose rows are full of
-// hits does not serialise the latency of its unions.  Every hit is counted; edges past
-// the list's capacity are left to tri_union_rows_kernel.
+// A lane whose eight entries lie in one row tests them against the bound table T with
+// any_hit8; a lane across a row end, or at the triangle's partial end, is a candidate
+// too.  Only when some lane is a candidate does the warp work out exact hit masks (entry
+// by entry, following the rows) and append the hits to an edge list with one atomic.
+// The unions run afterwards one edge per thread, so a warp whose rows are full of hits
+// does not serialise the latency of its unions.  Every hit is counted; edges past the
+// list's capacity are left to tri_union_rows_kernel.  Row and column indices are 32-bit
+// (n < 2^32).
 __global__ void __launch_bounds__(256)
-tri_hits_stream_kernel(const uint16_t *__restrict__ tri, const uint16_t *__restrict__ T, uint64_t n,
+tri_hits_stream_kernel(const uint16_t *__restrict__ tri, const uint16_t *__restrict__ T, uint32_t n,
                        uint64_t m, uint2 *edges, uint64_t cap, unsigned long long *count)
 {
     const uint64_t warp_id = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -311,51 +394,79 @@ tri_hits_stream_kernel(const uint16_t *__restrict__ tri, const uint16_t *__restr
     const uint64_t per = (spans + nwarps - 1) / nwarps;
     const uint64_t s0 = warp_id * per, s1 = min(spans, s0 + per);
     if (s0 >= s1) return;                      // warp-uniform
-    uint64_t i = 0, j = 1;
+    const uint64_t full_end = min(s1, m / 256);   // spans [s0, full_end) hold 256 entries
+    uint32_t i = 0, j = 1;
     const uint64_t k_first = s0 * 256 + 8 * lane;
-    if (k_first < m) tri_unindex(k_first, n, i, j);
-    const uint4 *t4 = reinterpret_cast<const uint4 *>(tri);
+    if (k_first < m) {
+        uint64_t ii, jj;
+        tri_unindex(k_first, n, ii, jj);
+        i = (uint32_t)ii;
+        j = (uint32_t)jj;
+    }
+    const uint4 *p = reinterpret_cast<const uint4 *>(tri) + s0 * 32 + lane;
     uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
-    if (k_first + 8 <= m) nxt = __ldg(t4 + k_first / 8);
+    if (s0 < full_end) nxt = __ldg(p);
     for (uint64_t sp = s0; sp < s1; ++sp) {
-        const uint64_t kb = sp * 256 + 8 * lane;
         uint32_t w[4] = {nxt.x, nxt.y, nxt.z, nxt.w};
-        if (sp + 1 < s1 && kb + 256 + 8 <= m) nxt = __ldg(t4 + (kb + 256) / 8);
-        uint32_t hm = 0;
-        if (kb + 8 <= m && j + 7 < n) {
-            hm = hits8(w, T[i], T, j);
-        } else if (kb < m) {
-            if (kb + 8 > m) {                  // the triangle's last, partial vector
-                w[0] = w[1] = w[2] = w[3] = 0u;
-                for (uint64_t e = 0; kb + e < m; ++e) w[e >> 1] |= (uint32_t)tri[kb + e] << (16 * (e & 1));
-            }
-            uint64_t ii = i, jj = j;
-            uint32_t ti = T[i];
-            for (int e = 0; e < 8 && kb + e < m; ++e) {
-                const uint32_t d = (w[e >> 1] >> (16 * (e & 1))) & 0xffffu;
-                if (d <= max(ti, (uint32_t)T[jj])) hm |= 1u << e;
-                if (++jj == n) { ++ii; jj = ii + 1; ti = T[ii]; }
-            }
-        }
-        if (__any_sync(0xffffffffu, hm != 0)) {
-            unsigned long long slot = warp_reserve(count, __popc(hm));
-            uint64_t ii = i, jj = j;
-            for (int e = 0; e < 8 && hm; ++e) {
-                if ((hm >> e) & 1u) {
-                    if (slot < cap) edges[slot] = make_uint2((uint32_t)ii, (uint32_t)jj);
-                    ++slot;
-                    hm &= ~(1u << e);
+        p += 32;
+        if (sp + 1 < full_end) nxt = __ldg(p);
+        const bool full = sp < full_end;
+        bool cand;
+        if (!full) cand = sp * 256 + 8 * lane < m;     // the triangle's partial last span
+        else if ((uint64_t)j + 7 >= n) cand = true;     // the lane's entries cross a row end
+        else cand = any_hit8(w, T[i], T, j);
+        if (__any_sync(0xffffffffu, cand)) {
+            const uint64_t kb = sp * 256 + 8 * lane;
+            uint32_t hm = 0;
+            if (cand) {
+                // entries e < 4 in lo, the rest in hi (64-bit shifts keep w in registers)
+                uint64_t lo = (uint64_t)w[1] << 32 | w[0], hi = (uint64_t)w[3] << 32 | w[2];
+                if (!full) {                   // the triangle's last, partial vector
+                    lo = hi = 0;
+                    for (uint64_t e = 0; kb + e < m; ++e) {
+                        const uint64_t v = tri[kb + e];
+                        if (e < 4) lo |= v << (16 * e);
+                        else hi |= v << (16 * (e - 4));
+                    }
                 }
-                if (++jj == n) { ++ii; jj = ii + 1; }
+                uint32_t ii = i, jj = j, ti = T[i];
+                for (int e = 0; e < 8 && kb + e < m; ++e) {
+                    const uint32_t d = (uint32_t)(((e < 4) ? lo : hi) >> (16 * (e & 3))) & 0xffffu;
+                    if (d <= max(ti, (uint32_t)T[jj])) hm |= 1u << e;
+                    if (++jj == n) { ++ii; jj = ii + 1; ti = T[ii]; }
+                }
+            }
+            if (__any_sync(0xffffffffu, hm != 0)) {
+                unsigned long long slot = warp_reserve(count, __popc(hm));
+                uint32_t ii = i, jj = j;
+                for (int e = 0; e < 8 && hm; ++e) {
+                    if ((hm >> e) & 1u) {
+                        if (slot < cap) edges[slot] = make_uint2(ii, jj);
+                        ++slot;
+                        hm &= ~(1u << e);
+                    }
+                    if (++jj == n) { ++ii; jj = ii + 1; }
+                }
             }
         }
-        tri_advance(i, j, 256, n);
+        // advance by one span (256 entries), across row ends
+        j += 256;
+        while (j >= n && i + 2 < n) {
+            const uint32_t over = j - n;
+            ++i;
+            j = i + 1 + over;
+        }
     }
 }
 
-// Hooks every read of an edge's larger end under its smallest neighbour (atomicMin):
-// a valid starting forest (links point to smaller reads of the same component) that
-// leaves the unions little to do.
+// Pre-hooks the larger end y of each edge (x, y), x < y, under x before the unions run.
+// On a fresh forest (every read its own root, FRESH) y goes under its smallest neighbour
+// (atomicMin): every link is then an edge of the graph, and all edges are unioned next,
+// so no connection is lost.  On a forest that earlier unions have built, a link may stand
+// for an edge no longer in any list, so only a root is hooked (compare-and-swap from
+// itself), which is an ordinary union step.  Either way links point to smaller reads of
+// the same component.
+template <bool FRESH>
 __global__ void min_hook_kernel(const uint2 *__restrict__ edges, uint64_t cap, const unsigned long long *count,
                                 uint32_t *parent)
 {
@@ -363,7 +474,8 @@ __global__ void min_hook_kernel(const uint2 *__restrict__ edges, uint64_t cap, c
     const uint64_t e_end = ne < cap ? ne : cap;
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e_end; e += (uint64_t)gridDim.x * blockDim.x) {
         const uint2 ed = edges[e];            // ed.x < ed.y
-        atomicMin(parent + ed.y, ed.x);
+        if (FRESH) atomicMin(parent + ed.y, ed.x);
+        else atomicCAS(parent + ed.y, ed.y, ed.x);
     }
 }
 
@@ -420,6 +532,13 @@ int check_launch(const char *what)
 
 }  // namespace
 
+// The rectangle kernel counts work units and a row's vectors in 32 bits.
+static bool rect_units_fit(uint64_t rows, uint64_t nb)
+{
+    const uint64_t nseg = ((nb + 7) / 8 + kRectSegVec - 1) / kRectSegVec;
+    return nb / 8 < (1ull << 32) && rows * nseg < (1ull << 32);
+}
+
 int launch_rect_epilogue(const uint16_t *out, uint64_t ld, const DeviceReads &A, uint64_t a0, uint64_t a1,
                          const DeviceReads &B, uint64_t b0, uint64_t b1, const Threshold &th, uint32_t *hits,
                          uint64_t cap, unsigned long long *count, const int32_t *col_labels,
@@ -427,19 +546,98 @@ int launch_rect_epilogue(const uint16_t *out, uint64_t ld, const DeviceReads &A,
 {
     if (a1 <= a0 || b1 <= b0) return GBD_OK;
     if (!count && !(row_labels && col_labels)) return GBD_OK;
-    const uint64_t nb = b1 - b0, nb_pad = nb + 16;
+    if (!rect_units_fit(a1 - a0, b1 - b0)) return fail(GBD_EINVAL, "rectangle too large for one epilogue pass");
+    // bounds of columns b0 - toff .. b1 - 1 (toff makes the table's first word hold an
+    // even column, so its 32-bit loads are aligned), zero padding after
+    const uint64_t nb = b1 - b0;
+    const uint32_t toff = (uint32_t)(b0 & 1);
+    const uint64_t nt = nb + toff, nt_pad = nt + 16;
     uint16_t *TB = nullptr;
-    GBD_CUDA_TRY(cudaMallocAsync((void **)&TB, nb_pad * sizeof(uint16_t), st));
-    hit_bound_kernel<<<grid_of((nb_pad + 255) / 256, sm_count, 8), 256, 0, st>>>(B.len + b0, nb, nb_pad, th, TB);
+    GBD_CUDA_TRY(cudaMallocAsync((void **)&TB, nt_pad * sizeof(uint16_t), st));
+    hit_bound_kernel<<<grid_of((nt_pad + 255) / 256, sm_count, 8), 256, 0, st>>>(B.len + (b0 - toff), nt, nt_pad, th,
+                                                                                  TB);
     int rc = check_launch("hit_bound_kernel launch");
     if (rc == GBD_OK) {
         const uint64_t nseg = ((nb + 7) / 8 + kRectSegVec - 1) / kRectSegVec;
-        rect_epilogue_kernel<<<grid_of((a1 - a0) * nseg, sm_count, 8), 256, 0, st>>>(
-            out, ld, A.len, a0, a1, TB, b0, nb, th, hits, cap, count, col_labels,
-            row_labels && col_labels ? row_labels : nullptr);
+        const RectOut o{hits, nullptr, cap, count, col_labels, row_labels && col_labels ? row_labels : nullptr};
+        rect_epilogue_kernel<<<grid_of((a1 - a0) * nseg, sm_count, 8), 256, 0, st>>>(out, ld, false, A.len, a0, a1,
+                                                                                      TB, toff, b0, nb, th, o);
         rc = check_launch("rect_epilogue_kernel launch");
     }
     cudaFreeAsync(TB, st);
+    return rc;
+}
+
+int band_forest_begin(BandForest &bf, const DeviceReads &S, const Threshold &th, uint32_t *parent, uint64_t max_entries,
+                      int sm_count, cudaStream_t st)
+{
+    const uint64_t n = S.n;
+    bf = BandForest{};
+    bf.cap = std::max<uint64_t>(1, std::min<uint64_t>(max_entries, kEdgeCap));
+    iota_kernel<<<grid_of((n + 255) / 256, sm_count, 16), 256, 0, st>>>(parent, n);
+    int rc = check_launch("iota_kernel launch");
+    if (rc != GBD_OK) return rc;
+    GBD_CUDA_TRY(cudaMallocAsync((void **)&bf.T, (n + 16) * sizeof(uint16_t), st));
+    GBD_CUDA_TRY(cudaMallocAsync((void **)&bf.edges, bf.cap * sizeof(uint2), st));
+    GBD_CUDA_TRY(cudaMallocAsync((void **)&bf.cnt, 2 * sizeof(unsigned long long), st));
+    GBD_CUDA_TRY(cudaMemsetAsync(bf.cnt, 0, 2 * sizeof(unsigned long long), st));
+    hit_bound_kernel<<<grid_of((n + 16 + 255) / 256, sm_count, 8), 256, 0, st>>>(S.len, n, n + 16, th, bf.T);
+    return check_launch("hit_bound_kernel launch");
+}
+
+int band_forest_add(BandForest &bf, const uint16_t *rect, uint64_t ld, const DeviceReads &S, uint64_t a0, uint64_t a1,
+                    const Threshold &th, uint32_t *parent, int sm_count, cudaStream_t st)
+{
+    const uint64_t n = S.n;
+    if (a1 <= a0 || a0 + 1 >= n) return GBD_OK;
+    const uint64_t b0 = a0 + 1, nb = n - b0;
+    if (!rect_units_fit(a1 - a0, nb)) return fail(GBD_EINVAL, "band too large for one epilogue pass");
+    const uint32_t toff = (uint32_t)(b0 & 1);
+    const uint64_t nseg = ((nb + 7) / 8 + kRectSegVec - 1) / kRectSegVec;
+    const RectOut o{nullptr, bf.edges, bf.cap, bf.cnt, nullptr, nullptr};
+    rect_epilogue_kernel<<<grid_of((a1 - a0) * nseg, sm_count, 8), 256, 0, st>>>(rect, ld, true, S.len, a0, a1,
+                                                                                  bf.T + (b0 - toff), toff, b0, nb, th, o);
+    int rc = check_launch("rect_epilogue_kernel launch");
+    const int eg = grid_of((bf.cap + 255) / 256, sm_count, 16);
+    if (rc == GBD_OK) {
+        if (bf.first) min_hook_kernel<true><<<eg, 256, 0, st>>>(bf.edges, bf.cap, bf.cnt, parent);
+        else min_hook_kernel<false><<<eg, 256, 0, st>>>(bf.edges, bf.cap, bf.cnt, parent);
+        rc = check_launch("min_hook_kernel launch");
+    }
+    if (rc == GBD_OK) {
+        union_edges_kernel<<<eg, 256, 0, st>>>(bf.edges, bf.cap, bf.cnt, parent);
+        rc = check_launch("union_edges_kernel launch");
+    }
+    if (rc == GBD_OK) {
+        band_union_rows_kernel<<<grid_of(a1 - a0, sm_count, 8), 256, 0, st>>>(rect, ld, bf.T, a0, a1, b0, nb, parent,
+                                                                                bf.cnt, bf.cap);
+        rc = check_launch("band_union_rows_kernel launch");
+    }
+    if (rc == GBD_OK) {
+        band_total_kernel<<<1, 1, 0, st>>>(bf.cnt, bf.cnt + 1);
+        rc = check_launch("band_total_kernel launch");
+    }
+    bf.first = false;
+    return rc;
+}
+
+int band_forest_end(BandForest &bf, uint32_t *parent, uint64_t n, unsigned long long *count, int sm_count,
+                    cudaStream_t st)
+{
+    int rc = GBD_OK;
+    if (bf.cnt) {
+        flatten_kernel<<<grid_of((n + 255) / 256, sm_count, 16), 256, 0, st>>>(parent, n);
+        rc = check_launch("flatten_kernel launch");
+        if (rc == GBD_OK && count) {
+            const cudaError_t e = cudaMemcpyAsync(count, bf.cnt + 1, sizeof(unsigned long long),
+                                                  cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync");
+        }
+    }
+    if (bf.T) cudaFreeAsync(bf.T, st);
+    if (bf.edges) cudaFreeAsync(bf.edges, st);
+    if (bf.cnt) cudaFreeAsync(bf.cnt, st);
+    bf = BandForest{};
     return rc;
 }
 
@@ -466,13 +664,13 @@ int launch_tri_components(const uint16_t *tri, const DeviceReads &S, const Thres
             hit_bound_kernel<<<grid_of((n + 16 + 255) / 256, sm_count, 8), 256, 0, st>>>(S.len, n, n + 16, th, T);
             rc = check_launch("hit_bound_kernel launch");
             if (rc == GBD_OK) {
-                tri_hits_stream_kernel<<<grid_of((m + 255) / 256, sm_count, 8), 256, 0, st>>>(tri, T, n, m, edges, cap,
-                                                                                               cnt);
+                tri_hits_stream_kernel<<<grid_of((m + 255) / 256, sm_count, 8), 256, 0, st>>>(tri, T, (uint32_t)n, m,
+                                                                                               edges, cap, cnt);
                 rc = check_launch("tri_hits_stream_kernel launch");
             }
             cudaFreeAsync(T, st);
             if (rc == GBD_OK) {
-                min_hook_kernel<<<grid_of((cap + 255) / 256, sm_count, 16), 256, 0, st>>>(edges, cap, cnt, parent);
+                min_hook_kernel<true><<<grid_of((cap + 255) / 256, sm_count, 16), 256, 0, st>>>(edges, cap, cnt, parent);
                 rc = check_launch("min_hook_kernel launch");
             }
             if (rc == GBD_OK) {

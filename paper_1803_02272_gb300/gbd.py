@@ -28,7 +28,7 @@ PROBE_OPS = ["VIMAX3_S16X2_RELU", "VIADDMAX_S16X2", "VIADDMAX_S16X2_RELU", "VIMA
 
 # every symbol include/gbd.h declares (checked by the tests)
 EXPORTS = [
-    "gbd_default_params", "gbd_create", "gbd_destroy", "gbd_load_reads", "gbd_free_set",
+    "gbd_default_params", "gbd_params_size", "gbd_create", "gbd_destroy", "gbd_load_reads", "gbd_free_set",
     "gbd_set_size", "gbd_set_max_len", "gbd_set_pair_cells", "gbd_all_pairs", "gbd_tile",
     "gbd_batch", "gbd_server_create", "gbd_server_submit", "gbd_server_poll",
     "gbd_server_wait", "gbd_server_destroy", "gbd_last_error", "gbd_probe_op_rate",
@@ -42,7 +42,8 @@ class GbdParams(ctypes.Structure):
     _fields_ = [("match", ctypes.c_int16), ("mismatch", ctypes.c_int16),
                 ("gap", ctypes.c_int16), ("conversion", ctypes.c_int16),
                 ("kernel", ctypes.c_int32), ("hbm_budget", ctypes.c_uint64),
-                ("timeout_us", ctypes.c_uint32), ("gap_open", ctypes.c_int16)]
+                ("timeout_us", ctypes.c_uint32), ("gap_open", ctypes.c_int16),
+                ("band_entries", ctypes.c_uint64)]
 
 
 class GbdThreshold(ctypes.Structure):
@@ -61,6 +62,7 @@ def _declare(lib):
     pp = ctypes.POINTER(ctypes.c_void_p)
     sig = {
         "gbd_default_params": ([ctypes.POINTER(GbdParams)], None),
+        "gbd_params_size": ([], u64),
         "gbd_create": ([pp, ci, ctypes.POINTER(GbdParams)], ci),
         "gbd_destroy": ([vp], None),
         "gbd_load_reads": ([vp, vp, vp, u64, pp, vp], ci),
@@ -136,6 +138,10 @@ def _stream(s) -> int:
 
 
 # ------------------------------------------------------------------ C names
+
+def gbd_params_size() -> int:
+    return _lib.gbd_params_size()
+
 
 def gbd_default_params() -> GbdParams:
     p = GbdParams()

@@ -44,8 +44,10 @@ def test_binding_lists_every_symbol():
 
 def test_default_params_and_errors_without_gpu():
     from paper_1803_02272_gb300 import gbd
+    assert gbd.gbd_params_size() == ctypes.sizeof(gbd.GbdParams)
     p = gbd.gbd_default_params()
     assert (p.match, p.mismatch, p.gap, p.conversion, p.kernel) == (1, -1, 1, 0, 0)
+    assert (p.gap_open, p.band_entries, p.hbm_budget, p.timeout_us) == (0, 0, 0, 0)
     assert gbd.gbd_last_error() == ""
     bad = gbd.gbd_default_params()
     bad.gap = -1

@@ -118,9 +118,10 @@ def test_tile_hits_rejects(env, ref_and_queries):
         assert e.value.code == gbd.GBD_EINVAL
 
 
-def _components_case(env, rs, num, den, abs_max, kernel="auto", want_tri=False):
+def _components_case(env, rs, num, den, abs_max, kernel="auto", want_tri=False, band_entries=0):
     gbd, torch = env
-    ctx = _ctx(gbd, kernel)
+    k = {"auto": gbd.GBD_KERNEL_AUTO, "general": gbd.GBD_KERNEL_GENERAL}[kernel]
+    ctx = gbd.Context(0, kernel=k, band_entries=band_entries)
     s = ctx.load(rs)
     n = rs.n
     labels = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
@@ -299,3 +300,55 @@ def test_tri_components_synthetic_triangle(env, num, den, abs_max):
     assert len(e) > 100
     assert int(edges.cpu().numpy()[0]) == len(e)
     np.testing.assert_array_equal(labels.cpu().numpy().astype(np.int64), oth.components(n, e))
+
+
+@pytest.mark.parametrize("band_entries", [1, 2000, 40000])
+@pytest.mark.parametrize("num,den,abs_max", [(6, 100, 65535), (1, 1, 12)])
+def test_components_in_bands(env, band_entries, num, den, abs_max):
+    """Without a triangle the graph is built band by band (one row per band, a few rows,
+    bands that grow towards the end); labels and edge count as the oracle's."""
+    rs = _clustered_set(700, 75)
+    tri = oracle.all_pairs(rs)
+    lab, ne, _ = _components_case(env, rs, num, den, abs_max, band_entries=band_entries)
+    edges = oth.threshold_edges(tri, rs.lengths, num, den, abs_max)
+    assert len(edges) > 50
+    assert ne == len(edges)
+    np.testing.assert_array_equal(lab, oth.components(rs.n, edges))
+
+
+def test_components_in_bands_long_reads_and_general_kernel(env):
+    """Bands with rows longer than the systolic query limit (general kernel rows inside a
+    band), and the general kernel for whole bands."""
+    st = synth.Stream(809, 0)
+    base = synth.random_codes(st, (900,))
+    reads = []
+    for _ in range(80):
+        L = int(st.integers(300, 900, ()))
+        r = base[:L].copy()
+        flip = st.integers(0, L - 1, (int(L * 0.03),))
+        r[flip] = (r[flip] + 1) % 4
+        reads.append("".join("ACGT"[c] for c in r))
+    rs = synth.from_strings(reads)
+    tri = oracle.all_pairs(rs)
+    edges = oth.threshold_edges(tri, rs.lengths, 8, 100)
+    for kernel in ("auto", "general"):
+        lab, ne, _ = _components_case(env, rs, 8, 100, 65535, kernel, band_entries=500)
+        assert ne == len(edges)
+        np.testing.assert_array_equal(lab, oth.components(rs.n, edges))
+
+
+@pytest.mark.parametrize("banded", [False, True])
+def test_components_edge_list_overflow(env, banded):
+    """Every pair a hit (d <= max(la, lb) always holds): more than 64 Mi edges, so the
+    edge list overflows and direct unions over the distances take over.  The graph is
+    complete: one component labelled 0, n(n-1)/2 edges."""
+    gbd, torch = env
+    n = 12000
+    st = synth.Stream(813, 0)
+    rs = synth.from_strings(["".join("ACGT"[c] for c in synth.random_codes(st, (int(st.integers(8, 24, ())),)))
+                             for _ in range(n)])
+    m = n * (n - 1) // 2
+    assert m > 64 << 20
+    lab, ne, _ = _components_case(env, rs, 1, 1, 65535, want_tri=not banded)
+    assert ne == m
+    assert not lab.any()

@@ -74,3 +74,26 @@ def test_annotation_by_hand():
 def test_hits_rect():
     D = np.array([[0, 5], [3, 4]])
     assert th.hits_rect(D, [100, 100], [100, 100], 3, 100) == {(0, 0, 0), (1, 0, 3)}
+
+
+def test_rule_equals_per_read_bound_form():
+    """The GPU streams test d <= max(T[la], T[lb]) with T[L] = min(abs_max, floor(num*L/den),
+    65535), a rewrite that holds because T is non-decreasing in L.  Checked here against
+    the oracle's rule on random rules, lengths and distances at the boundary."""
+    st = synth.Stream(4242, 0)
+    k = 20000
+    num = st.integers(0, (1 << 20) - 1, (k,))
+    den = st.integers(1, (1 << 20) - 1, (k,))
+    am = st.integers(0, 70000, (k,))
+    la, lb = st.integers(0, 65535, (k,)), st.integers(0, 65535, (k,))
+
+    def bound(L):
+        return np.minimum(np.minimum(am, num * L // den), 65535)
+
+    edge = bound(np.maximum(la, lb))
+    d = np.where(st.uniform((k,)) < 0.5, st.integers(0, 65535, (k,)), np.clip(edge + st.integers(-2, 2, (k,)), 0, 65535))
+    want = np.array([th.is_hit(int(d[t]), int(la[t]), int(lb[t]), int(num[t]), int(den[t]), int(am[t]))
+                     for t in range(k)])
+    got = d <= np.maximum(bound(la), bound(lb))
+    np.testing.assert_array_equal(got, want)
+    assert want.sum() > k // 10
