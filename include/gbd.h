@@ -74,7 +74,8 @@ typedef struct {
                              mismatch -1, gap 1 and gap_open <= 1000 it runs on the
                              systolic kernel, otherwise on the general kernel. */
     uint64_t band_entries;/* scratch (uint16 entries) of gbd_threshold_components when it
-                             holds no triangle; 0 = 2^28 (512 MB) */
+                             holds no triangle; 0 = 2^28 (512 MB); never less than one
+                             row (n - 1 entries) */
 } gbd_params;
 
 /* Fills *p with the defaults above. */

@@ -701,7 +701,8 @@ int gbd_threshold_components(gbd_ctx *ctx, const gbd_set *set, const gbd_thresho
     // bands of rows whose distances fit a bounded scratch: each band is computed, its hits
     // joined into the forest, and the scratch reused
     const uint64_t budget = ctx->params.band_entries ? ctx->params.band_entries : kBandEntries;
-    const uint64_t scratch = std::max<uint64_t>(1, std::min<uint64_t>(budget, n * (n - 1)));
+    // at least one whole row (the longest, n - 1 entries), so every band fits
+    const uint64_t scratch = std::max<uint64_t>(n - 1, std::min<uint64_t>(budget, n * (n - 1)));
     uint16_t *rect = nullptr;
     BandForest bf;
     if (m > 0) GBD_CUDA_TRY(cudaMallocAsync((void **)&rect, scratch * sizeof(uint16_t), st));
@@ -709,6 +710,10 @@ int gbd_threshold_components(gbd_ctx *ctx, const gbd_set *set, const gbd_thresho
     for (uint64_t a0 = 0; rc == GBD_OK && a0 + 1 < n;) {
         const uint64_t ld = n - a0 - 1;              // columns a0 + 1 .. n - 1
         const uint64_t a1 = std::min<uint64_t>(n - 1, a0 + std::max<uint64_t>(1, scratch / ld));
+        if ((a1 - a0) * ld > scratch) {
+            rc = fail(GBD_EINVAL, "gbd_threshold_components: band larger than its scratch");
+            break;
+        }
         rc = band_impl(ctx, set, a0, a1, rect, ld, st);
         if (rc == GBD_OK) rc = band_forest_add(bf, rect, ld, set->view(), a0, a1, t, d_labels, ctx->sm_count, st);
         a0 = a1;
