@@ -85,7 +85,10 @@ void gbd_default_params(gbd_params *p);
 uint64_t gbd_params_size(void);
 
 /* Creates a context on CUDA device `device` (made current on the calling thread).
- * p == NULL selects the defaults.  EINVAL on a negative gap or bad enum values. */
+ * p == NULL selects the defaults.  EINVAL on a negative gap or bad enum values.  The
+ * library's scratch is stream-ordered (cudaMallocAsync from the device's default pool);
+ * gbd_create raises that pool's release threshold to 4 GiB if it is lower, so scratch is
+ * reused across calls instead of being unmapped at every synchronisation. */
 int gbd_create(gbd_ctx **out, int device, const gbd_params *p);
 void gbd_destroy(gbd_ctx *ctx);
 

@@ -473,6 +473,18 @@ int gbd_create(gbd_ctx **out, int device, const gbd_params *p)
         delete ctx;
         return cuda_fail(e, "gbd_create");
     }
+    // Scratch comes from the device's default stream-ordered pool; with its default
+    // release threshold (0) every synchronisation hands the memory back and the next call
+    // maps it again (milliseconds for the 512 MB edge list).  Keep up to 4 GiB reserved
+    // (only ever raised, never lowered).
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = 0;
+        const uint64_t want = 4ull << 30;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess && keep < want)
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, (void *)&want);
+    }
+    cudaGetLastError();
     *out = ctx;
     return GBD_OK;
 }

@@ -78,8 +78,10 @@ __global__ void hit_bound_kernel(const uint16_t *__restrict__ len, uint64_t n, u
 // Hit mask of eight distances of one row (w: two per word, the first in the low half)
 // against the row's bound ti and the column bounds T[j .. j+7]: bit e set when entry e
 // is a hit.  Two entries per instruction: the column bounds arrive as packed pairs (a
-// 16-bit funnel shift when j is odd), the per-pair bound is a packed max and the test a
-// packed unsigned <=.  T must be 4-byte aligned with T[j + 9] readable.
+// 16-bit funnel shift when j is odd), the per-pair bound is a packed 3-way max and the
+// test a packed min that also yields (d <= bound) per half as predicates (DPX
+// instructions on this GPU; the older SIMD video intrinsics are emulated in software).
+// T must be 4-byte aligned with T[j + 9] readable.
 __device__ __forceinline__ uint32_t hits8(const uint32_t w[4], uint32_t ti, const uint16_t *__restrict__ T, uint64_t j)
 {
     const uint32_t *Tw = reinterpret_cast<const uint32_t *>(T) + (j >> 1);
@@ -92,33 +94,11 @@ __device__ __forceinline__ uint32_t hits8(const uint32_t w[4], uint32_t ti, cons
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const uint32_t t = __funnelshift_r(W[k], W[k + 1], sh);
-        const uint32_t c = __vsetleu2(w[k], __vmaxu2(ti2, t));     // 1 in each half that is a hit
-        m |= ((c | (c >> 15)) & 3u) << (2 * k);
+        bool hi, lo;
+        (void)__vibmin_u16x2(w[k], __vimax3_u16x2(ti2, t, t), &hi, &lo);
+        m |= ((uint32_t)lo | ((uint32_t)hi << 1)) << (2 * k);
     }
     return m;
-}
-
-// Whether any of the eight entries of hits8 is a hit, at six instructions per two
-// entries: where an entry is a hit its packed minimum with the bound equals the entry,
-// so (min ^ d) has a zero half there, and (x - 0x00010001) & ~x sets bit 15 of some half
-// exactly when x has a zero half (a borrow out of a zero low half can only add a flag
-// to the high half, never remove one).
-__device__ __forceinline__ bool any_hit8(const uint32_t w[4], uint32_t ti, const uint16_t *__restrict__ T, uint64_t j)
-{
-    const uint32_t *Tw = reinterpret_cast<const uint32_t *>(T) + (j >> 1);
-    const uint32_t sh = (uint32_t)(j & 1) * 16u;
-    uint32_t W[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) W[k] = __ldg(Tw + k);
-    const uint32_t ti2 = ti * 0x10001u;
-    uint32_t acc = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t t = __funnelshift_r(W[k], W[k + 1], sh);
-        const uint32_t x = __vminu2(w[k], __vmaxu2(ti2, t)) ^ w[k];
-        acc |= (x - 0x00010001u) & ~x;
-    }
-    return (acc & 0x80008000u) != 0;
 }
 
 // Reserves `cnt` consecutive slots for each lane of a full warp with one atomic: returns
@@ -244,15 +224,14 @@ rect_epilogue_kernel(const uint16_t *__restrict__ out, uint64_t ld, bool band, c
         for (uint32_t vb = v0 + warp * 32; vb < v1; vb += blockDim.x) {
             const uint32_t v = vb + lane;
             uint32_t w[4] = {0u, 0u, 0u, 0u};
-            bool cand = false;
+            uint32_t hm = 0;
             if (v < v1) {
                 const uint4 x = __ldg(pv + v);
                 w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
-                cand = any_hit8(w, ti, tbv, 8 * v + par);
+                hm = hits8(w, ti, tbv, 8 * v + par);
             }
-            if (!__any_sync(0xffffffffu, cand)) continue;
+            if (!__any_sync(0xffffffffu, hm != 0)) continue;
             const uint64_t c = rs.head + 8 * (uint64_t)v;
-            uint32_t hm = cand ? hits8(w, ti, TB, tb + c) : 0u;
             unsigned long long slot = want_hits ? warp_reserve(o.count, __popc(hm)) : 0;
             const uint64_t lo = (uint64_t)w[1] << 32 | w[0], hi = (uint64_t)w[3] << 32 | w[2];
             while (hm) {
@@ -411,14 +390,15 @@ tri_hits_stream_kernel(const uint16_t *__restrict__ tri, const uint16_t *__restr
         p += 32;
         if (sp + 1 < full_end) nxt = __ldg(p);
         const bool full = sp < full_end;
-        bool cand;
-        if (!full) cand = sp * 256 + 8 * lane < m;     // the triangle's partial last span
-        else if ((uint64_t)j + 7 >= n) cand = true;     // the lane's entries cross a row end
-        else cand = any_hit8(w, T[i], T, j);
-        if (__any_sync(0xffffffffu, cand)) {
+        // slow: the triangle's partial last span, or entries that cross a row end
+        bool slow;
+        uint32_t hm = 0;
+        if (!full) slow = sp * 256 + 8 * lane < m;
+        else if ((uint64_t)j + 7 >= n) slow = true;
+        else { slow = false; hm = hits8(w, T[i], T, j); }
+        if (__any_sync(0xffffffffu, slow || hm != 0)) {
             const uint64_t kb = sp * 256 + 8 * lane;
-            uint32_t hm = 0;
-            if (cand) {
+            if (slow) {
                 // entries e < 4 in lo, the rest in hi (64-bit shifts keep w in registers)
                 uint64_t lo = (uint64_t)w[1] << 32 | w[0], hi = (uint64_t)w[3] << 32 | w[2];
                 if (!full) {                   // the triangle's last, partial vector
