@@ -191,14 +191,23 @@ __global__ void colsum_partial_kernel(const float *__restrict__ X, uint64_t n, u
     }
 }
 
-__global__ void colmean_final_kernel(const double *__restrict__ partial, uint32_t nparts, uint32_t k, uint64_t n,
-                                     double *mean)
+// mean[c] = (sum of the partial sums of column c) / n: one block per column, a strided
+// sum per thread and a tree in shared memory (a fixed order, so the result is
+// reproducible).
+__global__ void __launch_bounds__(256)
+colmean_final_kernel(const double *__restrict__ partial, uint32_t nparts, uint32_t k, uint64_t n, double *mean)
 {
-    for (uint32_t c = threadIdx.x; c < k; c += blockDim.x) {
-        double s = 0.0;
-        for (uint32_t b = 0; b < nparts; ++b) s += partial[(uint64_t)b * k + c];
-        mean[c] = s / (double)n;
+    __shared__ double red[256];
+    const uint32_t c = blockIdx.x;
+    double s = 0.0;
+    for (uint32_t b = threadIdx.x; b < nparts; b += blockDim.x) s += partial[(uint64_t)b * k + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (uint32_t w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) mean[c] = red[0] / (double)n;
 }
 
 // Xt[c][i] = fp16(X[i][c] - mean[c]) for i < n; 0 for n <= i < ld.  32 x 32 tiles.
@@ -251,23 +260,38 @@ constexpr int kGramRows = 32;
 
 // partial[b] = sum over block b's rows of A[i]^T B[i] (k x k), float64 products of the
 // float32 inputs (exact) summed in a fixed order.  Rows are staged in shared memory as
-// float64; each thread owns 4 x 4 tiles of the output in registers.
+// float64; each thread owns 4 x 4 tiles of the output in registers.  With A == B (SYM)
+// only the tiles on or above the diagonal are accumulated and each is written to both
+// halves: float64 arithmetic is scarce on this GPU, and the Gram matrix is symmetric.
+template <bool SYM>
 __global__ void __launch_bounds__(256)
 xty_partial_kernel(const float *__restrict__ A, const float *__restrict__ B, uint64_t n, uint32_t k,
                    double *partial)
 {
     extern __shared__ double smd[];
-    double *As = smd;                       // [kGramRows][k]
-    double *Bs = smd + kGramRows * k;       // [kGramRows][k]
+    double *As = smd;                                 // [kGramRows][k]
+    double *Bs = SYM ? smd : smd + kGramRows * k;     // [kGramRows][k]
     const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
     const uint64_t r0 = blockIdx.x * per, r1 = std::min<uint64_t>(n, r0 + per);
     const uint32_t kt = k / 4;              // 4 x 4 tiles per side
-    const uint32_t ntiles = kt * kt;
+    const uint32_t ntiles = SYM ? kt * (kt + 1) / 2 : kt * kt;
     double *out = partial + (uint64_t)blockIdx.x * k * k;
     for (uint32_t t0 = 0; t0 < ntiles; t0 += blockDim.x) {
         const uint32_t t = t0 + threadIdx.x;
         const bool active = t < ntiles;
-        const uint32_t a0 = active ? (t / kt) * 4 : 0, b0 = active ? (t % kt) * 4 : 0;
+        uint32_t ta = 0, tb = 0;
+        if (active) {
+            if (SYM) {
+                // t-th tile of the upper triangle, row by row: row ta holds tiles ta .. kt-1
+                uint32_t rest = t;
+                while (rest >= kt - ta) { rest -= kt - ta; ++ta; }
+                tb = ta + rest;
+            } else {
+                ta = t / kt;
+                tb = t % kt;
+            }
+        }
+        const uint32_t a0 = ta * 4, b0 = tb * 4;
         double acc[4][4];
 #pragma unroll
         for (int x = 0; x < 4; ++x)
@@ -278,7 +302,7 @@ xty_partial_kernel(const float *__restrict__ A, const float *__restrict__ B, uin
             __syncthreads();
             for (uint32_t e = threadIdx.x; e < rows * k; e += blockDim.x) {
                 As[e] = (double)A[rb * k + e];
-                Bs[e] = (double)B[rb * k + e];
+                if (!SYM) Bs[e] = (double)B[rb * k + e];
             }
             __syncthreads();
             if (active) {
@@ -300,7 +324,10 @@ xty_partial_kernel(const float *__restrict__ A, const float *__restrict__ B, uin
 #pragma unroll
             for (int x = 0; x < 4; ++x)
 #pragma unroll
-                for (int y = 0; y < 4; ++y) out[(a0 + x) * k + b0 + y] = acc[x][y];
+                for (int y = 0; y < 4; ++y) {
+                    out[(a0 + x) * k + b0 + y] = acc[x][y];
+                    if (SYM && ta != tb) out[(b0 + y) * k + a0 + x] = acc[x][y];
+                }
         }
     }
 }
@@ -393,8 +420,11 @@ jacobi_kernel(const double *__restrict__ S_in, uint32_t k, uint32_t r, float *__
               float *__restrict__ lambda, uint32_t *flags)
 {
     extern __shared__ float sf[];
-    float *A = sf;                    // k x k
-    float *V = sf + k * k;            // k x k
+    // rows padded to k + 1 floats: a column walk (fixed p, rows 0..k-1) then falls in
+    // different banks instead of one
+    const uint32_t la = k + 1;
+    float *A = sf;                    // k x la
+    float *V = sf + k * la;           // k x la
     __shared__ float cs[kMaxJacobiK / 2], sn[kMaxJacobiK / 2];
     __shared__ int pp[kMaxJacobiK / 2], qq[kMaxJacobiK / 2];
     __shared__ double red[256];
@@ -406,8 +436,8 @@ jacobi_kernel(const double *__restrict__ S_in, uint32_t k, uint32_t r, float *__
     for (uint32_t e = threadIdx.x; e < kk; e += blockDim.x) {
         const uint32_t i = e / k, j = e % k;
         const double a = 0.5 * (S_in[i * k + j] + S_in[j * k + i]);
-        A[e] = (float)a;
-        V[e] = (i == j) ? 1.f : 0.f;
+        A[i * la + j] = (float)a;
+        V[i * la + j] = (i == j) ? 1.f : 0.f;
         tot += a * a;
         if (!isfinite(a)) atomicOr(flags, 2u);
     }
@@ -431,7 +461,7 @@ jacobi_kernel(const double *__restrict__ S_in, uint32_t k, uint32_t r, float *__
                 auto at = [&](uint32_t pos) -> uint32_t { return pos == 0 ? 0u : 1u + (pos - 1 + round) % (k - 1); };
                 uint32_t p = at(threadIdx.x), q = at(k - 1 - threadIdx.x);
                 if (p > q) { const uint32_t t = p; p = q; q = t; }
-                const float apq = A[p * k + q], app = A[p * k + p], aqq = A[q * k + q];
+                const float apq = A[p * la + q], app = A[p * la + p], aqq = A[q * la + q];
                 float c = 1.f, s = 0.f;
                 // negligible against the matrix norm (float32 cannot resolve less)
                 if (fabsf(apq) > fro_floor) {
@@ -458,12 +488,12 @@ jacobi_kernel(const double *__restrict__ S_in, uint32_t k, uint32_t r, float *__
                 if (s == 0.f) continue;
                 const int p = pp[pr], q = qq[pr];
                 const float c = cs[pr];
-                const float ap = A[row * k + p], aq = A[row * k + q];
-                A[row * k + p] = c * ap - s * aq;
-                A[row * k + q] = s * ap + c * aq;
-                const float vp = V[row * k + p], vq = V[row * k + q];
-                V[row * k + p] = c * vp - s * vq;
-                V[row * k + q] = s * vp + c * vq;
+                const float ap = A[row * la + p], aq = A[row * la + q];
+                A[row * la + p] = c * ap - s * aq;
+                A[row * la + q] = s * ap + c * aq;
+                const float vp = V[row * la + p], vq = V[row * la + q];
+                V[row * la + p] = c * vp - s * vq;
+                V[row * la + q] = s * vp + c * vq;
             }
             __syncthreads();
             // rows: A <- P^T A
@@ -473,9 +503,9 @@ jacobi_kernel(const double *__restrict__ S_in, uint32_t k, uint32_t r, float *__
                 if (s == 0.f) continue;
                 const int p = pp[pr], q = qq[pr];
                 const float c = cs[pr];
-                const float ap = A[p * k + col], aq = A[q * k + col];
-                A[p * k + col] = c * ap - s * aq;
-                A[q * k + col] = s * ap + c * aq;
+                const float ap = A[p * la + col], aq = A[q * la + col];
+                A[p * la + col] = c * ap - s * aq;
+                A[q * la + col] = s * ap + c * aq;
             }
             __syncthreads();
         }
@@ -485,10 +515,10 @@ jacobi_kernel(const double *__restrict__ S_in, uint32_t k, uint32_t r, float *__
     if (!converged && threadIdx.x == 0) atomicOr(flags, 1u);
     // eigenvalues on the diagonal; rank them largest first (ties by index)
     for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
-        const float li = A[i * k + i];
+        const float li = A[i * la + i];
         int rank = 0;
         for (uint32_t j = 0; j < k; ++j) {
-            const float lj = A[j * k + j];
+            const float lj = A[j * la + j];
             if (lj > li || (lj == li && j < i)) ++rank;
         }
         order[rank] = (int)i;
@@ -497,10 +527,10 @@ jacobi_kernel(const double *__restrict__ S_in, uint32_t k, uint32_t r, float *__
     for (uint32_t e = threadIdx.x; e < k * r; e += blockDim.x) {
         const uint32_t row = e / r, a = e % r;
         const int col = order[a];
-        const float lam = A[col * k + col];
-        T[e] = V[row * k + col] * sqrtf(fmaxf(lam, 0.f));
+        const float lam = A[col * la + col];
+        T[e] = V[row * la + col] * sqrtf(fmaxf(lam, 0.f));
     }
-    for (uint32_t a = threadIdx.x; a < r; a += blockDim.x) lambda[a] = A[order[a] * k + order[a]];
+    for (uint32_t a = threadIdx.x; a < r; a += blockDim.x) lambda[a] = A[order[a] * la + order[a]];
 }
 
 // ------------------------------------------------------------------ Out = A T
@@ -601,7 +631,7 @@ int column_means(const float *X, uint64_t n, uint32_t k, MdsWork &w)
 {
     colsum_partial_kernel<<<kSumBlocks, 128, 0, w.st>>>(X, n, k, w.sums);
     GBD_LAUNCH_CHECK("colsum_partial_kernel");
-    colmean_final_kernel<<<1, 128, 0, w.st>>>(w.sums, kSumBlocks, k, n, w.mean);
+    colmean_final_kernel<<<k, 256, 0, w.st>>>(w.sums, kSumBlocks, k, n, w.mean);
     GBD_LAUNCH_CHECK("colmean_final_kernel");
     return GBD_OK;
 }
@@ -629,7 +659,8 @@ int gram_apply_in(const uint16_t *W, int32_t shift, const float *X, float *Y, Md
 int xty(const float *A, const float *B, MdsWork &w)
 {
     const size_t smem = 2 * (size_t)kGramRows * w.k * sizeof(double);
-    xty_partial_kernel<<<w.gram_blocks, 256, smem, w.st>>>(A, B, w.n, w.k, w.gram_part);
+    if (A == B) xty_partial_kernel<true><<<w.gram_blocks, 256, smem, w.st>>>(A, B, w.n, w.k, w.gram_part);
+    else xty_partial_kernel<false><<<w.gram_blocks, 256, smem, w.st>>>(A, B, w.n, w.k, w.gram_part);
     GBD_LAUNCH_CHECK("xty_partial_kernel");
     xty_final_kernel<<<(w.k * w.k + 255) / 256, 256, 0, w.st>>>(w.gram_part, w.gram_blocks, w.k * w.k, w.gram);
     GBD_LAUNCH_CHECK("xty_final_kernel");
@@ -637,7 +668,7 @@ int xty(const float *A, const float *B, MdsWork &w)
 }
 
 size_t jacobi_smem(uint32_t k) { return 2 * (size_t)k * k * sizeof(double); }
-size_t jacobi_smem_f32(uint32_t k) { return 2 * (size_t)k * k * sizeof(float); }
+size_t jacobi_smem_f32(uint32_t k) { return 2 * (size_t)k * (k + 1) * sizeof(float); }
 
 int apply(const float *A, const float *T, uint32_t m, float *Out, MdsWork &w)
 {
@@ -680,7 +711,9 @@ int configure_kernels()
     if (done) return GBD_OK;
     GBD_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)jacobi_smem_f32(kMaxJacobiK)));
-    GBD_CUDA_TRY(cudaFuncSetAttribute(xty_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GBD_CUDA_TRY(cudaFuncSetAttribute(xty_partial_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(2 * kGramRows * kMaxJacobiK * sizeof(double))));
+    GBD_CUDA_TRY(cudaFuncSetAttribute(xty_partial_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(2 * kGramRows * kMaxJacobiK * sizeof(double))));
     GBD_CUDA_TRY(cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)jacobi_smem(kMaxJacobiK)));

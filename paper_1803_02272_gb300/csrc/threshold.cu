@@ -503,6 +503,19 @@ int grid_of(uint64_t work, int sm_count, int per_sm)
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(work, (uint64_t)std::max(sm_count, 1) * per_sm));
 }
 
+// One resident wave of `kernel` (blocks of 256 threads): the streams give every block
+// (or warp) an equal share up front, so a partial second wave would double their time.
+template <typename K>
+int resident_grid(K kernel, int sm_count, uint64_t work)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return grid_of(work, sm_count, per_sm);
+}
+
 int check_launch(const char *what)
 {
     note_launches(1);
@@ -540,7 +553,8 @@ int launch_rect_epilogue(const uint16_t *out, uint64_t ld, const DeviceReads &A,
     if (rc == GBD_OK) {
         const uint64_t nseg = ((nb + 7) / 8 + kRectSegVec - 1) / kRectSegVec;
         const RectOut o{hits, nullptr, cap, count, col_labels, row_labels && col_labels ? row_labels : nullptr};
-        rect_epilogue_kernel<<<grid_of((a1 - a0) * nseg, sm_count, 8), 256, 0, st>>>(out, ld, false, A.len, a0, a1,
+        rect_epilogue_kernel<<<resident_grid(rect_epilogue_kernel, sm_count, (a1 - a0) * nseg), 256, 0, st>>>(
+            out, ld, false, A.len, a0, a1,
                                                                                       TB, toff, b0, nb, th, o);
         rc = check_launch("rect_epilogue_kernel launch");
     }
@@ -575,7 +589,8 @@ int band_forest_add(BandForest &bf, const uint16_t *rect, uint64_t ld, const Dev
     const uint32_t toff = (uint32_t)(b0 & 1);
     const uint64_t nseg = ((nb + 7) / 8 + kRectSegVec - 1) / kRectSegVec;
     const RectOut o{nullptr, bf.edges, bf.cap, bf.cnt, nullptr, nullptr};
-    rect_epilogue_kernel<<<grid_of((a1 - a0) * nseg, sm_count, 8), 256, 0, st>>>(rect, ld, true, S.len, a0, a1,
+    rect_epilogue_kernel<<<resident_grid(rect_epilogue_kernel, sm_count, (a1 - a0) * nseg), 256, 0, st>>>(
+        rect, ld, true, S.len, a0, a1,
                                                                                   bf.T + (b0 - toff), toff, b0, nb, th, o);
     int rc = check_launch("rect_epilogue_kernel launch");
     const int eg = grid_of((bf.cap + 255) / 256, sm_count, 16);
@@ -644,7 +659,8 @@ int launch_tri_components(const uint16_t *tri, const DeviceReads &S, const Thres
             hit_bound_kernel<<<grid_of((n + 16 + 255) / 256, sm_count, 8), 256, 0, st>>>(S.len, n, n + 16, th, T);
             rc = check_launch("hit_bound_kernel launch");
             if (rc == GBD_OK) {
-                tri_hits_stream_kernel<<<grid_of((m + 255) / 256, sm_count, 8), 256, 0, st>>>(tri, T, (uint32_t)n, m,
+                tri_hits_stream_kernel<<<resident_grid(tri_hits_stream_kernel, sm_count, (m + 255) / 256), 256, 0, st>>>(
+                    tri, T, (uint32_t)n, m,
                                                                                                edges, cap, cnt);
                 rc = check_launch("tri_hits_stream_kernel launch");
             }
