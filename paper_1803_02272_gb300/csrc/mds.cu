@@ -258,19 +258,38 @@ __global__ void center_scale_kernel(const float *__restrict__ P, const double *_
 // ------------------------------------------------------------------ A^T B in float64
 constexpr int kGramRows = 32;
 
-// partial[b] = sum over block b's rows of A[i]^T B[i] (k x k), float64 products of the
-// float32 inputs (exact) summed in a fixed order.  Rows are staged in shared memory as
-// float64; each thread owns 4 x 4 tiles of the output in registers.  With A == B (SYM)
-// only the tiles on or above the diagonal are accumulated and each is written to both
-// halves: float64 arithmetic is scarce on this GPU, and the Gram matrix is symmetric.
+// a * b = p + e and s + h = t + f exactly (the product split with a fused multiply-add,
+// the sum by Knuth's two-sum); the _rn intrinsics keep the compiler from contracting
+// or reassociating these steps.
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+__device__ __forceinline__ void two_sum(float s, float h, float &t, float &f)
+{
+    t = __fadd_rn(s, h);
+    const float bp = __fsub_rn(t, s);
+    f = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(h, bp));
+}
+
+// partial[b] = sum over block b's rows of A[i]^T B[i] (k x k) for float32 A, B.  Each
+// product is split exactly into two floats and added to a two-float running sum (the
+// high part by an exact two-sum, the low part collecting the rounding terms), which
+// carries about 48 bits, close to float64 accumulation, at float32 instruction rates
+// (float64 arithmetic runs about 60 times slower on this GPU).  Fixed summation order.
+// Rows are staged in shared memory; each thread owns 4 x 4 tiles of the output in
+// registers.  With A == B (SYM) only the tiles on or above the diagonal are accumulated
+// and each is written to both halves.
 template <bool SYM>
 __global__ void __launch_bounds__(256)
 xty_partial_kernel(const float *__restrict__ A, const float *__restrict__ B, uint64_t n, uint32_t k,
                    double *partial)
 {
-    extern __shared__ double smd[];
-    double *As = smd;                                 // [kGramRows][k]
-    double *Bs = SYM ? smd : smd + kGramRows * k;     // [kGramRows][k]
+    extern __shared__ float smf[];
+    float *As = smf;                                 // [kGramRows][k]
+    float *Bs = SYM ? smf : smf + kGramRows * k;     // [kGramRows][k]
     const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
     const uint64_t r0 = blockIdx.x * per, r1 = std::min<uint64_t>(n, r0 + per);
     const uint32_t kt = k / 4;              // 4 x 4 tiles per side
@@ -292,31 +311,35 @@ xty_partial_kernel(const float *__restrict__ A, const float *__restrict__ B, uin
             }
         }
         const uint32_t a0 = ta * 4, b0 = tb * 4;
-        double acc[4][4];
+        float hi[4][4], lo[4][4];
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) acc[x][y] = 0.0;
+            for (int y = 0; y < 4; ++y) { hi[x][y] = 0.f; lo[x][y] = 0.f; }
         for (uint64_t rb = r0; rb < r1; rb += kGramRows) {
             const uint32_t rows = (uint32_t)std::min<uint64_t>(kGramRows, r1 - rb);
             __syncthreads();
             for (uint32_t e = threadIdx.x; e < rows * k; e += blockDim.x) {
-                As[e] = (double)A[rb * k + e];
-                if (!SYM) Bs[e] = (double)B[rb * k + e];
+                As[e] = A[rb * k + e];
+                if (!SYM) Bs[e] = B[rb * k + e];
             }
             __syncthreads();
             if (active) {
                 for (uint32_t r = 0; r < rows; ++r) {
-                    const double2 a01 = *reinterpret_cast<const double2 *>(As + r * k + a0);
-                    const double2 a23 = *reinterpret_cast<const double2 *>(As + r * k + a0 + 2);
-                    const double2 b01 = *reinterpret_cast<const double2 *>(Bs + r * k + b0);
-                    const double2 b23 = *reinterpret_cast<const double2 *>(Bs + r * k + b0 + 2);
-                    const double av[4] = {a01.x, a01.y, a23.x, a23.y};
-                    const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
+                    const float4 a4 = *reinterpret_cast<const float4 *>(As + r * k + a0);
+                    const float4 b4 = *reinterpret_cast<const float4 *>(Bs + r * k + b0);
+                    const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+                    const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
                     for (int x = 0; x < 4; ++x)
 #pragma unroll
-                        for (int y = 0; y < 4; ++y) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
+                        for (int y = 0; y < 4; ++y) {
+                            float p, pe, t2, f;
+                            two_prod(av[x], bv[y], p, pe);
+                            two_sum(hi[x][y], p, t2, f);
+                            hi[x][y] = t2;
+                            lo[x][y] = __fadd_rn(lo[x][y], __fadd_rn(f, pe));
+                        }
                 }
             }
         }
@@ -325,8 +348,9 @@ xty_partial_kernel(const float *__restrict__ A, const float *__restrict__ B, uin
             for (int x = 0; x < 4; ++x)
 #pragma unroll
                 for (int y = 0; y < 4; ++y) {
-                    out[(a0 + x) * k + b0 + y] = acc[x][y];
-                    if (SYM && ta != tb) out[(b0 + y) * k + a0 + x] = acc[x][y];
+                    const double v = (double)hi[x][y] + (double)lo[x][y];
+                    out[(a0 + x) * k + b0 + y] = v;
+                    if (SYM && ta != tb) out[(b0 + y) * k + a0 + x] = v;
                 }
         }
     }
@@ -355,6 +379,7 @@ chol_inverse_kernel(const double *__restrict__ S_in, uint32_t k, double floor_re
     double *Ti = sc + k * k;        // k x k, R^-1
     __shared__ double smax;
     __shared__ int keep[128];
+    __shared__ double inv_d[128];
     const uint32_t kk = k * k;
     for (uint32_t e = threadIdx.x; e < kk; e += blockDim.x) {
         const uint32_t i = e / k, j = e % k;
@@ -380,23 +405,33 @@ chol_inverse_kernel(const double *__restrict__ S_in, uint32_t k, double floor_re
             R[j * k + c] = ok ? (c == j ? rjj : R[j * k + c] / rjj) : 0.0;
         if (threadIdx.x == 0) keep[j] = ok;
         __syncthreads();
-        // trailing update A[r][c] -= R[j][r] R[j][c], j < r <= c
-        const uint32_t m = k - 1 - j;
-        for (uint32_t e = threadIdx.x; e < m * m; e += blockDim.x) {
-            const uint32_t r = j + 1 + e / m, c = j + 1 + e % m;
-            if (c >= r) R[r * k + c] -= R[j * k + r] * R[j * k + c];
+        // trailing update A[r][c] -= R[j][r] R[j][c], j < r <= c: warps over rows, lanes
+        // over columns
+        const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (uint32_t r = j + 1 + warp; r < k; r += nw) {
+            const double rjr = R[j * k + r];
+            for (uint32_t c = r + lane; c < k; c += 32) R[r * k + c] -= rjr * R[j * k + c];
         }
         __syncthreads();
     }
-    // T = R^-1 column by column (back substitution; dropped rows stay 0)
+    // T = R^-1 column by column (back substitution; dropped rows stay 0), with the
+    // reciprocals of the diagonal formed once and two partial sums per dot product
+    // (float64 division and dependent float64 chains are slow on this GPU)
+    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) inv_d[i] = keep[i] ? 1.0 / R[i * k + i] : 0.0;
+    __syncthreads();
     for (uint32_t c = threadIdx.x; c < k; c += blockDim.x) {
         if (!keep[c]) continue;
-        Ti[c * k + c] = 1.0 / R[c * k + c];
+        Ti[c * k + c] = inv_d[c];
         for (int i = (int)c - 1; i >= 0; --i) {
             if (!keep[i]) continue;
-            double s = 0.0;
-            for (uint32_t m2 = (uint32_t)i + 1; m2 <= c; ++m2) s += R[i * k + m2] * Ti[m2 * k + c];
-            Ti[i * k + c] = -s / R[i * k + i];
+            double s0 = 0.0, s1 = 0.0;
+            uint32_t m2 = (uint32_t)i + 1;
+            for (; m2 + 1 <= c; m2 += 2) {
+                s0 += R[i * k + m2] * Ti[m2 * k + c];
+                s1 += R[i * k + m2 + 1] * Ti[(m2 + 1) * k + c];
+            }
+            if (m2 <= c) s0 += R[i * k + m2] * Ti[m2 * k + c];
+            Ti[i * k + c] = -(s0 + s1) * inv_d[i];
         }
     }
     __syncthreads();
@@ -658,7 +693,7 @@ int gram_apply_in(const uint16_t *W, int32_t shift, const float *X, float *Y, Md
 
 int xty(const float *A, const float *B, MdsWork &w)
 {
-    const size_t smem = 2 * (size_t)kGramRows * w.k * sizeof(double);
+    const size_t smem = 2 * (size_t)kGramRows * w.k * sizeof(float);
     if (A == B) xty_partial_kernel<true><<<w.gram_blocks, 256, smem, w.st>>>(A, B, w.n, w.k, w.gram_part);
     else xty_partial_kernel<false><<<w.gram_blocks, 256, smem, w.st>>>(A, B, w.n, w.k, w.gram_part);
     GBD_LAUNCH_CHECK("xty_partial_kernel");
@@ -712,9 +747,9 @@ int configure_kernels()
     GBD_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)jacobi_smem_f32(kMaxJacobiK)));
     GBD_CUDA_TRY(cudaFuncSetAttribute(xty_partial_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(2 * kGramRows * kMaxJacobiK * sizeof(double))));
+                                      (int)(2 * kGramRows * kMaxJacobiK * sizeof(float))));
     GBD_CUDA_TRY(cudaFuncSetAttribute(xty_partial_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(2 * kGramRows * kMaxJacobiK * sizeof(double))));
+                                      (int)(2 * kGramRows * kMaxJacobiK * sizeof(float))));
     GBD_CUDA_TRY(cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)jacobi_smem(kMaxJacobiK)));
     GBD_CUDA_TRY(cudaFuncSetAttribute(
