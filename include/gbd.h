@@ -92,6 +92,11 @@ uint64_t gbd_params_size(void);
 int gbd_create(gbd_ctx **out, int device, const gbd_params *p);
 void gbd_destroy(gbd_ctx *ctx);
 
+/* Frees what the context keeps between calls (the MDS square, the captured batch graph)
+ * after waiting for the device to finish its work.  The next call that needs them
+ * rebuilds them.  EINVAL on a NULL context. */
+int gbd_trim(gbd_ctx *ctx);
+
 /* Ingest (a1): copies (if host pointers) and packs n reads into a device-resident set:
  * 2-bit codes A=0 C=1 G=2 T=3, 16 bases per uint32 (base k of a word in bits 2k..2k+1),
  * a fixed stride of ceil(max_len/16) words per read, and per-read uint16 lengths.
@@ -250,9 +255,10 @@ int gbd_tri_components(gbd_ctx *ctx, const gbd_set *set, const uint16_t *d_tri, 
  *   d_lambda (device, r float32, largest first) and the n x r coordinates into d_coords
  *   (device, float32 row-major).  d_omega is the caller's n x k Gaussian test matrix
  *   (device, float32 row-major; the library draws no random numbers), r <= k, k as above,
- *   k < n, q >= 0 rounds.  The library allocates its workspace on `stream` (the fp16 square,
- *   ld^2 * 2 bytes with ld = n rounded up to 128 -- 20 GB at n = 1e5 -- plus O(n k)) and
- *   frees it before returning; ENOMEM if it does not fit.  The call synchronises `stream`
+ *   k < n, q >= 0 rounds.  Workspace: the fp16 square (ld^2 * 2 bytes with ld = n rounded
+ *   up to 128 -- 20 GB at n = 1e5) is kept in the context between calls and reused when
+ *   large enough (gbd_trim or gbd_destroy frees it); O(n k) more is allocated on `stream`
+ *   and freed before returning; ENOMEM if it does not fit.  The call synchronises `stream`
  *   at its end (it reads back convergence and error flags).  EINVAL on bad sizes. */
 int gbd_sqdist_square(gbd_ctx *ctx, const uint16_t *d_tri, uint64_t n, uint16_t *d_w, uint64_t ld,
                       int32_t *shift, void *stream);

@@ -494,6 +494,7 @@ void gbd_destroy(gbd_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     free_batch_cache(ctx);
+    free_mds_cache(ctx);
     for (cudaStream_t st : {ctx->aux, ctx->capture}) {
         if (st) {
             cudaStreamSynchronize(st);
@@ -503,6 +504,16 @@ void gbd_destroy(gbd_ctx *ctx)
     if (ctx->fork) cudaEventDestroy(ctx->fork);
     if (ctx->join) cudaEventDestroy(ctx->join);
     delete ctx;
+}
+
+int gbd_trim(gbd_ctx *ctx)
+{
+    if (!ctx) return fail(GBD_EINVAL, "gbd_trim: NULL context");
+    GBD_CUDA_TRY(cudaSetDevice(ctx->device));
+    GBD_CUDA_TRY(cudaDeviceSynchronize());
+    free_batch_cache(ctx);
+    free_mds_cache(ctx);
+    return GBD_OK;
 }
 
 int gbd_load_reads(gbd_ctx *ctx, const uint8_t *seq, const uint64_t *offsets, uint64_t n,

@@ -80,6 +80,11 @@ struct gbd_ctx {
     cudaEvent_t fork = nullptr, join = nullptr;   // fork / join of aux with the caller's stream
     cudaStream_t capture = nullptr;   // stream that records batch graphs
     void *batch_cache = nullptr;      // last captured batch graph (api.cu)
+    // gbd_mds's fp16 square (ld^2 entries, 20 GB at n = 10^5), kept between calls: the
+    // stream-ordered pool would unmap it at every synchronisation and map it again (ms)
+    void *mds_w = nullptr;
+    size_t mds_w_bytes = 0;
+    cudaEvent_t mds_w_done = nullptr; // recorded after the last work that used mds_w
 };
 
 struct gbd_set {
@@ -175,6 +180,8 @@ int band_forest_end(BandForest &bf, uint32_t *parent, uint64_t n, unsigned long 
 
 // Frees the context's cached batch graph.
 void free_batch_cache(gbd_ctx *ctx);
+// Frees the context's cached MDS square (after its last use has finished).
+void free_mds_cache(gbd_ctx *ctx);
 
 // Instruction-rate probe.
 int probe_op_rate(int op, uint32_t iters, double *rate, int sm_count, cudaStream_t stream);

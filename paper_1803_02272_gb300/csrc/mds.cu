@@ -800,6 +800,33 @@ int sqdist_square_impl(gbd_ctx *ctx, const uint16_t *d_tri, uint64_t n, uint16_t
     return GBD_OK;
 }
 
+// The context's cached square of at least `bytes`, ordered after its previous use on any
+// stream.  A larger size replaces it (after the previous use has finished).
+int mds_square_buffer(gbd_ctx *ctx, size_t bytes, cudaStream_t st, uint16_t **W)
+{
+    if (!ctx->mds_w_done) GBD_CUDA_TRY(cudaEventCreateWithFlags(&ctx->mds_w_done, cudaEventDisableTiming));
+    if (ctx->mds_w_bytes < bytes) {
+        if (ctx->mds_w) {
+            GBD_CUDA_TRY(cudaEventSynchronize(ctx->mds_w_done));
+            GBD_CUDA_TRY(cudaFree(ctx->mds_w));
+            ctx->mds_w = nullptr;
+            ctx->mds_w_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&ctx->mds_w, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->mds_w = nullptr;
+            return fail(GBD_ENOMEM, std::string("MDS square of ") + std::to_string(bytes) + " bytes: " +
+                                        cudaGetErrorString(e));
+        }
+        ctx->mds_w_bytes = bytes;
+    } else {
+        GBD_CUDA_TRY(cudaStreamWaitEvent(st, ctx->mds_w_done, 0));
+    }
+    *W = static_cast<uint16_t *>(ctx->mds_w);
+    return GBD_OK;
+}
+
 int read_flags(MdsWork &w)
 {
     uint32_t h[2] = {0, 0};
@@ -816,6 +843,23 @@ int read_flags(MdsWork &w)
 }  // namespace gbd
 
 using namespace gbd;
+
+namespace gbd {
+void free_mds_cache(gbd_ctx *ctx)
+{
+    if (ctx->mds_w) {
+        if (ctx->mds_w_done) cudaEventSynchronize(ctx->mds_w_done);
+        cudaFree(ctx->mds_w);
+        ctx->mds_w = nullptr;
+        ctx->mds_w_bytes = 0;
+    }
+    if (ctx->mds_w_done) {
+        cudaEventDestroy(ctx->mds_w_done);
+        ctx->mds_w_done = nullptr;
+    }
+    cudaGetLastError();
+}
+}  // namespace gbd
 
 extern "C" int gbd_sqdist_square(gbd_ctx *ctx, const uint16_t *d_tri, uint64_t n, uint16_t *d_w, uint64_t ld,
                                  int32_t *shift, void *stream)
@@ -862,7 +906,7 @@ extern "C" int gbd_mds(gbd_ctx *ctx, const uint16_t *d_tri, uint64_t n, const fl
     float *Y = nullptr, *Q = nullptr;
     int32_t shift = 0;
     rc = w.init(n, ld, k, ctx->sm_count, st);
-    if (rc == GBD_OK) rc = w.alloc((void **)&W, (size_t)ld * ld * 2);
+    if (rc == GBD_OK) rc = mds_square_buffer(ctx, (size_t)ld * ld * 2, st, &W);
     if (rc == GBD_OK) rc = w.alloc((void **)&Y, (size_t)n * k * 4);
     if (rc == GBD_OK) rc = w.alloc((void **)&Q, (size_t)n * k * 4);
     if (rc == GBD_OK) rc = sqdist_square_impl(ctx, d_tri, n, W, ld, &shift, st);
@@ -883,6 +927,7 @@ extern "C" int gbd_mds(gbd_ctx *ctx, const uint16_t *d_tri, uint64_t n, const fl
         if (le != cudaSuccess) rc = cuda_fail(le, "jacobi_kernel launch");
     }
     if (rc == GBD_OK) rc = apply(Q, w.T, r, d_coords, w);
+    if (W) cudaEventRecord(ctx->mds_w_done, st);
     int frc = (rc == GBD_OK) ? read_flags(w) : rc;
     w.release();
     return frc;

@@ -28,7 +28,7 @@ PROBE_OPS = ["VIMAX3_S16X2_RELU", "VIADDMAX_S16X2", "VIADDMAX_S16X2_RELU", "VIMA
 
 # every symbol include/gbd.h declares (checked by the tests)
 EXPORTS = [
-    "gbd_default_params", "gbd_params_size", "gbd_create", "gbd_destroy", "gbd_load_reads", "gbd_free_set",
+    "gbd_default_params", "gbd_params_size", "gbd_create", "gbd_destroy", "gbd_trim", "gbd_load_reads", "gbd_free_set",
     "gbd_set_size", "gbd_set_max_len", "gbd_set_pair_cells", "gbd_all_pairs", "gbd_tile",
     "gbd_batch", "gbd_server_create", "gbd_server_submit", "gbd_server_poll",
     "gbd_server_wait", "gbd_server_destroy", "gbd_last_error", "gbd_probe_op_rate",
@@ -65,6 +65,7 @@ def _declare(lib):
         "gbd_params_size": ([], u64),
         "gbd_create": ([pp, ci, ctypes.POINTER(GbdParams)], ci),
         "gbd_destroy": ([vp], None),
+        "gbd_trim": ([vp], ci),
         "gbd_load_reads": ([vp, vp, vp, u64, pp, vp], ci),
         "gbd_free_set": ([vp], None),
         "gbd_set_size": ([vp], u64),
@@ -157,6 +158,11 @@ def gbd_create(device: int = 0, params: GbdParams | None = None) -> int:
 
 def gbd_destroy(ctx: int) -> None:
     _lib.gbd_destroy(ctx)
+
+
+def gbd_trim(ctx: int) -> None:
+    """Free the context's kept workspaces (MDS square, captured batch graph)."""
+    _check(_lib.gbd_trim(ctx))
 
 
 def gbd_load_reads(ctx: int, seq, offsets, n: int, stream=None) -> int:

@@ -237,3 +237,21 @@ def test_mds_rejects_bad_sizes(env, n, k, r, q):
     with pytest.raises(gbd.GbdError) as e:
         gbd.gbd_mds(ctx.handle, tri, n, om, k, r, q, lam, X)
     assert e.value.code == gbd.GBD_EINVAL
+
+
+def test_mds_kept_square_reused_grown_and_trimmed(env):
+    """The context keeps the fp16 square between calls: a smaller problem after a larger
+    one reuses it, a larger one replaces it, gbd_trim frees it; every call gives the same
+    result as the first call of its size (the arithmetic is deterministic)."""
+    gbd, ctx, torch = env
+    rng = np.random.default_rng(17)
+    small = rng.integers(1, 400, size=500 * 499 // 2).astype(np.uint16)
+    large = rng.integers(1, 400, size=900 * 899 // 2).astype(np.uint16)
+    first_small = _mds_case(env, small, 500, 32, 8, 1, 5)
+    first_large = _mds_case(env, large, 900, 32, 8, 1, 6)
+    again_small = _mds_case(env, small, 500, 32, 8, 1, 5)
+    gbd.gbd_trim(ctx.handle)
+    after_trim = _mds_case(env, large, 900, 32, 8, 1, 6)
+    for a, b in ((first_small, again_small), (first_large, after_trim)):
+        np.testing.assert_array_equal(a[0], b[0])
+        np.testing.assert_array_equal(a[1], b[1])
