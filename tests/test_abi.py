@@ -48,7 +48,6 @@ def test_default_params_and_errors_without_gpu():
     p = gbd.gbd_default_params()
     assert (p.match, p.mismatch, p.gap, p.conversion, p.kernel) == (1, -1, 1, 0, 0)
     assert (p.gap_open, p.band_entries, p.hbm_budget, p.timeout_us) == (0, 0, 0, 0)
-    assert gbd.gbd_last_error() == ""
     bad = gbd.gbd_default_params()
     bad.gap = -1
     with pytest.raises(gbd.GbdError) as ei:
