@@ -296,7 +296,12 @@ uint64_t gbd_kernel_launches(void);
 #define GBD_PROBE_MIX_DPX_HMAX2      16  /* half the chains DPX, half fp16x2 max */
 #define GBD_PROBE_MIX_DPX_FMAX3      17  /* half the chains DPX, half fp32 3-input max */
 #define GBD_PROBE_MIX_DPX_IADD3      18  /* half the chains DPX, half 3-input integer add */
-#define GBD_PROBE_COUNT              19
+#define GBD_PROBE_VIMAX3_U16X2       19  /* unsigned 16x2 3-input max (threshold bounds) */
+#define GBD_PROBE_VMINU2             20  /* unsigned 16x2 min, SIMD video form */
+#define GBD_PROBE_VSETLEU2           21  /* unsigned 16x2 <= to 0/1 per half, SIMD video form */
+#define GBD_PROBE_VIBMIN_U16X2       22  /* unsigned 16x2 min with per-half <= predicates, the
+                                            predicate of the high half added back (2 ops) */
+#define GBD_PROBE_COUNT              23
 int gbd_probe_op_rate(int op, uint32_t iters, double *lane_ops_per_s, void *stream);
 
 #ifdef __cplusplus

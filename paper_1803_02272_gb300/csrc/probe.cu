@@ -50,6 +50,13 @@ __device__ __forceinline__ uint32_t apply(uint32_t x, uint32_t y, uint32_t k)
         return __float_as_uint(d);
     } else if constexpr (OP == GBD_PROBE_FADD) {
         return __float_as_uint(__fadd_rn(__uint_as_float(x), __uint_as_float(y)));
+    } else if constexpr (OP == GBD_PROBE_VIMAX3_U16X2) return __vimax3_u16x2(x, y, k);
+    else if constexpr (OP == GBD_PROBE_VMINU2) return __vminu2(x, y);
+    else if constexpr (OP == GBD_PROBE_VSETLEU2) return __vsetleu2(x, y) ^ k;
+    else if constexpr (OP == GBD_PROBE_VIBMIN_U16X2) {
+        bool hi, lo;
+        const uint32_t m = __vibmin_u16x2(x, y, &hi, &lo);
+        return m + (uint32_t)hi;
     } else return x ^ y;
 }
 
@@ -161,6 +168,10 @@ int probe_op_rate(int op, uint32_t iters, double *rate, int sm_count, cudaStream
             case GBD_PROBE_MIX_DPX_HMAX2: launch_probe<GBD_PROBE_MIX_DPX_HMAX2>(blocks, it, sink, stream); break;
             case GBD_PROBE_MIX_DPX_FMAX3: launch_probe<GBD_PROBE_MIX_DPX_FMAX3>(blocks, it, sink, stream); break;
             case GBD_PROBE_MIX_DPX_IADD3: launch_probe<GBD_PROBE_MIX_DPX_IADD3>(blocks, it, sink, stream); break;
+            case GBD_PROBE_VIMAX3_U16X2: launch_probe<GBD_PROBE_VIMAX3_U16X2>(blocks, it, sink, stream); break;
+            case GBD_PROBE_VMINU2: launch_probe<GBD_PROBE_VMINU2>(blocks, it, sink, stream); break;
+            case GBD_PROBE_VSETLEU2: launch_probe<GBD_PROBE_VSETLEU2>(blocks, it, sink, stream); break;
+            case GBD_PROBE_VIBMIN_U16X2: launch_probe<GBD_PROBE_VIBMIN_U16X2>(blocks, it, sink, stream); break;
             case GBD_PROBE_CELL_MIX: probe_cell_kernel<<<blocks, 256, 0, stream>>>(it, 0x9e3779b9u, sink); break;
         }
     };

@@ -24,7 +24,7 @@ GBD_KERNEL_AUTO, GBD_KERNEL_GENERAL, GBD_KERNEL_SYSTOLIC = 0, 1, 2
 PROBE_OPS = ["VIMAX3_S16X2_RELU", "VIADDMAX_S16X2", "VIADDMAX_S16X2_RELU", "VIMAX_S16X2_RELU",
              "VMAXS2", "PRMT", "IADD3", "LOP3", "IMAX", "HMAX2", "HADD2", "CELL_MIX",
              "VIMAX3_S16X2", "FMAX", "FMAX3", "FADD", "MIX_DPX_HMAX2", "MIX_DPX_FMAX3",
-             "MIX_DPX_IADD3"]
+             "MIX_DPX_IADD3", "VIMAX3_U16X2", "VMINU2", "VSETLEU2", "VIBMIN_U16X2"]
 
 # every symbol include/gbd.h declares (checked by the tests)
 EXPORTS = [

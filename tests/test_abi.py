@@ -59,3 +59,14 @@ def test_default_params_and_errors_without_gpu():
 def test_library_is_sm103a_only():
     from paper_1803_02272_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_probe_op_names_match_header():
+    """The binding's probe names are the header's GBD_PROBE_* codes, in code order."""
+    from paper_1803_02272_gb300 import gbd
+    codes = {}
+    for m in re.finditer(r"#define GBD_PROBE_(\w+)\s+(\d+)", open(HEADER).read()):
+        codes[m.group(1)] = int(m.group(2))
+    count = codes.pop("COUNT")
+    assert sorted(codes.values()) == list(range(count))
+    assert [name for name, _ in sorted(codes.items(), key=lambda kv: kv[1])] == gbd.PROBE_OPS
