@@ -221,16 +221,9 @@ rect_epilogue_kernel(const uint16_t *__restrict__ out, uint64_t ld, bool band, c
         const uint64_t t0 = tb + rs.head;
         const uint16_t *tbv = TB + (t0 & ~1ull);
         const uint32_t par = (uint32_t)(t0 & 1);
-        for (uint32_t vb = v0 + warp * 32; vb < v1; vb += blockDim.x) {
-            const uint32_t v = vb + lane;
-            uint32_t w[4] = {0u, 0u, 0u, 0u};
-            uint32_t hm = 0;
-            if (v < v1) {
-                const uint4 x = __ldg(pv + v);
-                w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
-                hm = hits8(w, ti, tbv, 8 * v + par);
-            }
-            if (!__any_sync(0xffffffffu, hm != 0)) continue;
+        // the hits of one lane's vector v (mask hm, data w); called by the whole warp
+        auto take = [&](uint32_t v, const uint32_t w[4], uint32_t hm) {
+            if (!__any_sync(0xffffffffu, hm != 0)) return;
             const uint64_t c = rs.head + 8 * (uint64_t)v;
             unsigned long long slot = want_hits ? warp_reserve(o.count, __popc(hm)) : 0;
             const uint64_t lo = (uint64_t)w[1] << 32 | w[0], hi = (uint64_t)w[3] << 32 | w[2];
@@ -245,6 +238,20 @@ rect_epilogue_kernel(const uint16_t *__restrict__ out, uint64_t ld, bool band, c
                     if (sp >= 0) mine = label_join(mine, sp);
                 }
             }
+        };
+        // two vectors per lane per iteration (v and v + 32), both loads issued first
+        for (uint32_t vb = v0 + warp * 64; vb < v1; vb += 2 * blockDim.x) {
+            const uint32_t va = vb + lane, vc = vb + 32 + lane;
+            const bool oka = va < v1, okc = vc < v1;
+            uint4 xa = make_uint4(0u, 0u, 0u, 0u), xc = make_uint4(0u, 0u, 0u, 0u);
+            if (oka) xa = __ldg(pv + va);
+            if (okc) xc = __ldg(pv + vc);
+            const uint32_t wa[4] = {xa.x, xa.y, xa.z, xa.w}, wc[4] = {xc.x, xc.y, xc.z, xc.w};
+            const uint32_t ha = oka ? hits8(wa, ti, tbv, 8 * va + par) : 0u;
+            const uint32_t hc = okc ? hits8(wc, ti, tbv, 8 * vc + par) : 0u;
+            if (!__any_sync(0xffffffffu, (ha | hc) != 0)) continue;
+            take(va, wa, ha);
+            take(vc, wc, hc);
         }
         // entries before the first boundary and after the last vector: warp 0 of segment 0
         if (seg == 0 && warp == 0) {
