@@ -3,7 +3,7 @@
 // A distance d between reads of lengths la, lb is a hit when d <= abs_max and
 // d * den <= num * max(la, lb) (integer arithmetic; 97 % homology is num/den = 3/100).
 //   * rectangle (section 4.3, sample reads against annotated reference reads): hits are
-//     appended to a list through one atomic counter, and each row keeps the one species
+//     appended to a list (one atomic per warp on its counter), and each row keeps the one species
 //     of all its hits, -2 once two species disagree, -1 with no hit (references with a
 //     negative label do not vote);
 //   * triangle (section 5, the threshold graph): each hit (i, j) joins i and j in a
@@ -11,8 +11,8 @@
 //     component ends with its smallest read as the root; a last pass points every read
 //     at its root.
 // Both streams read each distance once with 16-byte loads and test it against a table of
-// per-read bounds (hit_bound, two entries per SIMD instruction), so they run at HBM speed
-// rather than at the speed of the integer test.
+// per-read bounds (hit_bound), two entries per packed 16-bit instruction instead of a
+// multiply-compare per entry.
 #include "gbd_internal.cuh"
 
 namespace gbd {
