@@ -256,10 +256,9 @@ def kernel_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(pairs: int):
-    """DRAM bytes per all-pairs launch, scaled from the committed ncu summary of a smaller
-    case (traffic is dominated by the uint16 output, i.e. grows with the pair count); None
-    once the kernel source differs from the profiled one."""
+def traffic_value(key: str):
+    """A per-pair DRAM figure from the committed ncu summary of the distance kernel, or
+    None once the kernel source differs from the profiled one."""
     try:
         kv = {}
         for line in open(TRAFFIC_FILE):
@@ -268,9 +267,26 @@ def traffic_per_launch(pairs: int):
                 kv[k.strip()] = v.strip().strip("`")
         if kv.get("kernel_sha") != kernel_sha():
             return None
-        return float(kv["dram_bytes_per_pair"]) * pairs
+        return float(kv[key])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def traffic_per_launch(pairs: int):
+    """DRAM bytes (read + write) per all-pairs launch: the per-pair figure of the committed
+    ncu summary (traffic is dominated by the uint16 output, so it grows with the pair
+    count) times the pairs; None once the kernel source differs from the profiled one."""
+    per_pair = traffic_value("dram_bytes_per_pair")
+    return None if per_pair is None else per_pair * pairs
+
+
+def triangle_write(pairs: int, seconds: float):
+    """HBM write rate of the triangle: the algorithmic 2 bytes per pair, and the DRAM
+    bytes written per pair in the committed ncu summary, over the kernel time."""
+    per_pair = traffic_value("dram_write_bytes_per_pair")
+    return {"algorithmic_gbs": 2.0 * pairs / seconds / 1e9,
+            "dram_gbs": None if per_pair is None else per_pair * pairs / seconds / 1e9,
+            "dram_bytes_per_pair": per_pair}
 
 
 def run_gbd(args):
@@ -371,6 +387,7 @@ def run_gbd(args):
                          "textbook_peak": peak["textbook_gcups"],
                          "textbook_frac": achieved / peak["textbook_gcups"],
                          "probe_lane_ops_per_s": peak["rates"]},
+            "triangle_write": triangle_write(m, kern_s),
             "clocks": clocks, "gpu_launches": int(launches), "spot_check": spot,
         }
     if not args.no_e2e and rank == 0:

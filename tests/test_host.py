@@ -49,3 +49,14 @@ def test_bench_reference_arm_prints_one_line():
     assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["cores"] >= 1
     assert rec["e2e"]["h2d_bytes_per_step"] == 0 and rec["e2e"]["d2h_bytes_per_step"] == 0
     assert rec["config"]["n_reads"] == 300
+
+
+def test_bench_triangle_write_and_traffic_figures():
+    sys.path.insert(0, ROOT)
+    import bench
+    tw = bench.triangle_write(10**9, 2.0)
+    assert tw["algorithmic_gbs"] == 1.0
+    per_pair = bench.traffic_value("dram_bytes_per_pair")
+    if per_pair is not None:          # the kernel sources still match the profiled ones
+        assert per_pair >= 2.0 and bench.traffic_per_launch(10) == per_pair * 10
+        assert tw["dram_bytes_per_pair"] >= 2.0
