@@ -159,12 +159,22 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle baseline
 
-def cpu_oracle_sample(rs, seconds: float, seed: int = 7):
-    """Time the CPU oracle on a bounded uniform sample of the workload's pairs."""
+# ------------------------------------------------------------------ the cpu_baseline leg
+# Every call into oracle/ that bench.py makes is in the functions below: each times the
+# oracle on a bounded sample of its mode's workload (the cpu_baseline figure) and, when
+# given the GPU's values for the same sample, compares them (the spot check).
+
+def _oracle_cores():
+    return os.cpu_count() or 1
+
+
+def cpu_oracle_sample(rs, seconds: float, seed: int = 7, gpu_pairs=None):
+    """Time the CPU oracle on a bounded uniform sample of the workload's pairs; with
+    gpu_pairs (a function (i, j) -> the GPU's distances) also compare the last sample."""
     import oracle
     n = rs.n
     L = rs.lengths.astype(np.float64)
-    cores = os.cpu_count() or 1
+    cores = _oracle_cores()
 
     def sample(k, s):
         st_rng = np.random.default_rng(s)
@@ -176,15 +186,95 @@ def cpu_oracle_sample(rs, seconds: float, seed: int = 7):
     for attempt in range(6):           # grow the sample until it takes about `seconds`
         i, j = sample(k, seed + attempt)
         t0 = time.perf_counter()
-        oracle.pairs(rs, i, j, nthreads=cores)
+        want = oracle.pairs(rs, i, j, nthreads=cores)
         dt = time.perf_counter() - t0
         if dt >= 0.5 * seconds or k >= 4_000_000:
             break
         k = int(min(4_000_000, max(2 * k, k * seconds / max(dt, 1e-6))))
     cells = float(np.sum(L[i] * L[j]))
+    out = {"value": cells / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{k} uniformly sampled pairs of the same {n}-read workload, "
+                     f"{cells:.3e} cells in {dt:.1f} s on {cores} host threads"}
+    if gpu_pairs is not None:
+        got = np.asarray(gpu_pairs(i, j), dtype=np.uint16)
+        out["check"] = {"pairs_checked": int(k), "mismatches": int(np.count_nonzero(got != want))}
+    return out
+
+
+def cpu_baseline_pairs(qs, i, j, ref=None, got=None, gap_open: int = 0, what: str = "pairs"):
+    """The oracle on given pairs (qs[i[t]], ref[j[t]]) (ref = qs if None), timed; compared
+    with the GPU's values `got` when given."""
+    import oracle
+    cores = _oracle_cores()
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    t0 = time.perf_counter()
+    want = oracle.pairs(qs, i, j, ref, nthreads=cores, gap_open=gap_open)
+    dt = max(time.perf_counter() - t0, 1e-9)
+    La = qs.lengths.astype(np.float64)[i]
+    Lb = (ref if ref is not None else qs).lengths.astype(np.float64)[j]
+    cells = float(np.sum(La * Lb))
+    out = {"value": cells / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{len(i)} sampled {what}, {cells:.3e} cells in {dt:.2f} s on {cores} host threads"}
+    if got is not None:
+        got = np.asarray(got, dtype=np.uint16)
+        out["check"] = {"pairs_checked": int(len(i)), "mismatches": int(np.count_nonzero(got != want))}
+    return out
+
+
+def cpu_baseline_components(rs, i, j, th, labels):
+    """The oracle's distances and hit rule on sampled pairs, timed; every sampled hit pair
+    must share a component of the GPU's labels, and every label must be a root."""
+    import oracle
+    from oracle import threshold as oth
+    cores = _oracle_cores()
+    t0 = time.perf_counter()
+    d = oracle.pairs(rs, i, j, nthreads=cores)
+    L = rs.lengths
+    hit = oth.is_hit(d, L[i], L[j], th.num, th.den, th.abs_max)
+    dt = max(time.perf_counter() - t0, 1e-9)
+    cells = float(np.sum(L[i].astype(np.float64) * L[j]))
+    n = len(labels)
     return {"value": cells / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{k} uniformly sampled pairs of the same {n}-read workload, "
-                      f"{cells:.3e} cells in {dt:.1f} s on {cores} host threads"}
+            "sample": f"{len(i)} uniformly sampled pairs with the hit rule, {dt:.2f} s on {cores} host threads",
+            "check": {"pairs_checked": int(len(i)), "hits": int(hit.sum()),
+                      "hit_pairs_split": int(np.count_nonzero(hit & (labels[i] != labels[j]))),
+                      "labels_are_roots": bool(np.all(labels[labels] == labels) and np.all(labels <= np.arange(n)))}}
+
+
+def cpu_baseline_annotate(qs, ref, ref_lab, th, got_rows):
+    """The oracle's rectangle and annotation rule for sample reads qs against ref, timed;
+    compared with the GPU's row labels for the same reads."""
+    import oracle
+    from oracle import threshold as oth
+    cores = _oracle_cores()
+    t0 = time.perf_counter()
+    D = oracle.rect(qs, 0, qs.n, ref, 0, ref.n, nthreads=cores)
+    want = oth.annotate(D, qs.lengths, ref.lengths, ref_lab, th.num, th.den, th.abs_max)
+    dt = max(time.perf_counter() - t0, 1e-9)
+    cells = float(qs.lengths.sum()) * float(ref.lengths.sum())
+    return {"value": cells / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{qs.n} sample reads against all {ref.n} references, annotated, {dt:.1f} s "
+                      f"on {cores} host threads",
+            "check": {"rows_checked": int(qs.n), "mismatches": int(np.count_nonzero(np.asarray(got_rows) != want))}}
+
+
+def cpu_baseline_mds(n_full: int, k: int, r: int, q: int, n_sample: int = 2000):
+    """Time the oracle's randomized MDS on an n_sample-read synthetic triangle; the
+    oracle forms G with two dense n x n products (O(n^3)), so the full-size figure is
+    extrapolated as n^3."""
+    from oracle import mds as omds
+    from paper_1803_02272_gb300 import synth
+    m = n_sample * (n_sample - 1) // 2
+    tri = synth.Stream(91, 0).integers(0, 450, (m,)).astype(np.uint16)
+    omega = synth.Stream(92, 0).normal((n_sample, k))
+    t0 = time.perf_counter()
+    omds.mds_randomized(omds.tri_to_square(tri, n_sample), r, omega, q)
+    dt = time.perf_counter() - t0
+    scale = (n_full / n_sample) ** 3
+    return {"value": dt * scale, "unit": "s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"oracle randomized MDS of a {n_sample}-read triangle (k={k}, r={r}, q={q}) "
+                      f"in {dt:.2f} s, extrapolated by (n/{n_sample})^3 to n={n_full}"}
 
 
 def run_reference(args):
@@ -353,18 +443,10 @@ def run_gbd(args):
     gcups = value_cps / 1e9
     pairs_per_s = m * args.steps * world / t_max
 
-    # exactness spot check of this very output: a seeded sample against the oracle
-    spot = None
-    if rank == 0:
-        import oracle
-        st = np.random.default_rng(99)
-        k = 2000
-        i = st.integers(0, n - 1, size=k)
-        j = i + 1 + (st.random(k) * (n - 1 - i)).astype(np.int64)
+    def gpu_pairs(i, j):
+        """The GPU triangle's distances of pairs (i, j), i < j."""
         idx = i * n - i * (i + 1) // 2 + (j - i - 1)
-        got = tri[torch.from_numpy(idx).to(dev)].cpu().numpy().view(np.uint16)
-        want = oracle.pairs(rs, i, j)
-        spot = {"pairs_checked": k, "mismatches": int(np.count_nonzero(got != want))}
+        return tri[torch.from_numpy(idx).to(dev)].cpu().numpy().view(np.uint16)
 
     line = None
     if rank == 0:
@@ -388,14 +470,16 @@ def run_gbd(args):
                          "textbook_frac": achieved / peak["textbook_gcups"],
                          "probe_lane_ops_per_s": peak["rates"]},
             "triangle_write": triangle_write(m, kern_s),
-            "clocks": clocks, "gpu_launches": int(launches), "spot_check": spot,
+            "clocks": clocks, "gpu_launches": int(launches), "spot_check": None,
         }
     if not args.no_e2e and rank == 0:
         line["e2e"] = run_e2e(gbd, ctx, rs, dev, stream)
     elif rank == 0:
         line["e2e"] = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        line["cpu_baseline"] = cpu_oracle_sample(rs, args.cpu_seconds)
+        # the oracle's sample doubles as an exactness check of this very triangle
+        line["cpu_baseline"] = cpu_oracle_sample(rs, args.cpu_seconds, gpu_pairs=gpu_pairs)
+        line["spot_check"] = line["cpu_baseline"].pop("check")
     if args.serve_requests > 0 and rank == 0:
         # served-batch latency: Poisson arrivals against this set, resident
         ref = ctx.load(rs)
@@ -471,12 +555,11 @@ def serve_phase(gbd, ctx, ref_handle, ref_rs, dev, n_requests, load=1.0, capacit
     wall = time.perf_counter() - t0
     srv.close()
     torch.cuda.synchronize()
-    mism = None
+    mism, base = None, None
     if check:
-        import oracle
+        # four sampled (row, reference) entries of every request, against the oracle
         rng = np.random.default_rng(seed)
-        pi, pj, got = [], [], []
-        q_all = []
+        pj, got, q_all = [], [], []
         for k, out in outs:
             q = reqs[k].reads
             rows = rng.integers(0, q.n, size=4)
@@ -488,15 +571,16 @@ def serve_phase(gbd, ctx, ref_handle, ref_rs, dev, n_requests, load=1.0, capacit
                 pj.append(int(c_))
                 got.append(int(v_))
         qs = synth.from_strings(q_all)
-        want = oracle.pairs(qs, np.arange(len(q_all)), np.array(pj), ref_rs)
-        mism = int(np.count_nonzero(want != np.array(got, dtype=np.uint16)))
+        base = cpu_baseline_pairs(qs, np.arange(len(q_all)), np.array(pj), ref_rs, got,
+                                  what="served (query, reference) pairs")
+        mism = base.pop("check")["mismatches"]
     del outs
     nq = [r.reads.n for r in reqs]
     return {"requests": len(reqs), "mean_queries": float(np.mean(nq)),
             "offered_load": None if burst else load, "rate_per_s": None if burst else rate_per_s,
             "p50_ms": percentile(lat, 50) * 1e3, "p99_ms": percentile(lat, 99) * 1e3,
             "pairs_per_s": total_pairs / wall, "wall_s": wall,
-            "spot_check_mismatches": mism}
+            "spot_check_mismatches": mism, "cpu_baseline": base}
 
 
 def run_batch_mode(args):
@@ -595,24 +679,6 @@ def run_serve_mode(args):
                                "server_vs_plain": small_burst["pairs_per_s"] / small_plain_pps}}
     print(json.dumps(line), flush=True)
     return 0
-
-
-def mds_cpu_sample(n_full: int, k: int, r: int, q: int, n_sample: int = 2000):
-    """Time the oracle's randomized MDS on an n_sample-read synthetic triangle; the
-    oracle forms G with two dense n x n products (O(n^3)), so the full-size figure is
-    extrapolated as n^3."""
-    from oracle import mds as omds
-    from paper_1803_02272_gb300 import synth
-    m = n_sample * (n_sample - 1) // 2
-    tri = synth.Stream(91, 0).integers(0, 450, (m,)).astype(np.uint16)
-    omega = synth.Stream(92, 0).normal((n_sample, k))
-    t0 = time.perf_counter()
-    omds.mds_randomized(omds.tri_to_square(tri, n_sample), r, omega, q)
-    dt = time.perf_counter() - t0
-    scale = (n_full / n_sample) ** 3
-    return {"value": dt * scale, "unit": "s", "cores": os.cpu_count() or 1, "kind": "oracle",
-            "sample": f"oracle randomized MDS of a {n_sample}-read triangle (k={k}, r={r}, q={q}) "
-                      f"in {dt:.2f} s, extrapolated by (n/{n_sample})^3 to n={n_full}"}
 
 
 def run_mds_mode(args):
@@ -733,7 +799,7 @@ def run_mds_mode(args):
                 "d2h_bytes_per_step": int(n * r * 4 + r * 4)},
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = mds_cpu_sample(n, k, r, q)
+        line["cpu_baseline"] = cpu_baseline_mds(n, k, r, q)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -781,19 +847,13 @@ def run_components_mode(args):
     t = float(np.mean(times))
     lab = labels.cpu().numpy().astype(np.int64)
     ne = int(edges.cpu().numpy()[0])
-    # sampled check against the oracle: every sampled hit pair shares a component; labels
-    # are roots (label[label[i]] == label[i] <= i)
-    import oracle
-    from oracle import threshold as oth
+    # sampled check against the oracle (the cpu_baseline leg): every sampled hit pair
+    # shares a component; labels are roots (label[label[i]] == label[i] <= i)
     rng = np.random.default_rng(5)
     i = rng.integers(0, n - 1, size=3000)
     j = i + 1 + (rng.random(3000) * (n - 1 - i)).astype(np.int64)
-    d = oracle.pairs(rs, i, j)
-    L = rs.lengths
-    hit = oth.is_hit(d, L[i], L[j], th.num, th.den, th.abs_max)
-    check = {"pairs_checked": 3000, "hits": int(hit.sum()),
-             "hit_pairs_split": int(np.count_nonzero(hit & (lab[i] != lab[j]))),
-             "labels_are_roots": bool(np.all(lab[lab] == lab) and np.all(lab <= np.arange(n)))}
+    base = cpu_baseline_components(rs, i, j, th, lab)
+    check = base.pop("check")
     # whole pipeline through the C ABI with host buffers: reads in, labels out
     seq_h = torch.from_numpy(rs.seq).pin_memory()
     off_h = torch.from_numpy(rs.offsets.view(np.int64)).pin_memory()
@@ -821,7 +881,7 @@ def run_components_mode(args):
                          "kernel": "tri_union_kernel + iota/flatten (one gbd_tri_components call)",
                          "peak_source": "of measured: MEASURED_PEAKS hbm_gbs (copy)"},
             "components": int(len(np.unique(lab))), "edges": ne, "clocks": clocks,
-            "gpu_launches": int(launches), "spot_check": check,
+            "gpu_launches": int(launches), "spot_check": check, "cpu_baseline": base,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(rs.seq.nbytes + rs.offsets.nbytes),
                     "d2h_bytes_per_step": int(n * 4), "note": "load + all-pairs + components, host labels"}}
     print(json.dumps(line), flush=True)
@@ -867,13 +927,14 @@ def run_affine_mode(args):
         times.append(e0.elapsed_time(e1) / 1e3)
     launches = (gbd.gbd_kernel_launches() - launches0) // max(args.steps, 1)
     clocks = sampler.stop()
-    import oracle
+    # 400 sampled pairs against the oracle's Gotoh mode (the cpu_baseline leg)
     rng = np.random.default_rng(11)
     i = rng.integers(0, n - 1, size=400)
     j = i + 1 + (rng.random(400) * (n - 1 - i)).astype(np.int64)
     idx = i * n - i * (i + 1) // 2 + (j - i - 1)
     got = tri[torch.from_numpy(idx).to(dev)].cpu().numpy().view(np.uint16)
-    want = oracle.pairs(rs, i, j, gap_open=args.gap_open)
+    base = cpu_baseline_pairs(rs, i, j, got=got, gap_open=args.gap_open, what="pairs with affine gaps")
+    check = base.pop("check")
     t = float(np.mean(times))
     rate = max(gbd.gbd_probe_op_rate(gbd.PROBE_OPS.index(nm), 20000, stream)
                for nm in ("VIMAX3_S16X2", "VIADDMAX_S16X2"))
@@ -887,7 +948,7 @@ def run_affine_mode(args):
                          "peak_source": "of measured: ALU-pipe issue rate (probe) x 2 cells / 4.5 ops "
                                         "(E, F and H add-max, 3-way max, half a 3-way max for the running max)"},
             "clocks": clocks, "gpu_launches": int(launches),
-            "spot_check": {"pairs_checked": 400, "mismatches": int(np.count_nonzero(got != want))},
+            "spot_check": check, "cpu_baseline": base,
             "e2e": None}
     print(json.dumps(line), flush=True)
     return 0
@@ -950,12 +1011,10 @@ def run_annotate_mode(args):
     tt = time.perf_counter() - t0
     n_hits = int(count.cpu().numpy()[0])
     lab = rows.cpu().numpy()
-    # sampled rows against the oracle's annotation
-    import oracle
-    from oracle import threshold as oth
+    # sampled rows against the oracle's annotation (the cpu_baseline leg)
     sel = np.arange(0, nq, 256)
-    D = oracle.rect(qs.subset(sel), 0, len(sel), ref, 0, nr)
-    want = oth.annotate(D, qs.lengths[sel], ref.lengths, ref_lab, th.num, th.den, th.abs_max)
+    base = cpu_baseline_annotate(qs.subset(sel), ref, ref_lab, th, lab[sel])
+    check = base.pop("check")
     bytes_alg = nq * nr * 2 + nr * 6
     hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
     line = {"metric": f"homology-gap annotation of {nq} reads against {nr} labelled references, rule {args.th}",
@@ -970,7 +1029,7 @@ def run_annotate_mode(args):
                          "peak_source": "of measured: MEASURED_PEAKS hbm_gbs (copy)"},
             "epilogue_ms": t_ep * 1e3, "hits": n_hits,
             "assigned": int((lab >= 0).sum()), "ambiguous": int((lab == -2).sum()), "unassigned": int((lab == -1).sum()),
-            "spot_check": {"rows_checked": int(len(sel)), "mismatches": int(np.count_nonzero(lab[sel] != want))},
+            "spot_check": check, "cpu_baseline": base,
             "clocks": clocks,
             "e2e": {"value": tt, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(nq * 4),
                     "note": "gbd_tile_hits: rectangle + epilogue on resident sets, labels to pinned host memory"}}

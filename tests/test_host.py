@@ -60,3 +60,61 @@ def test_bench_triangle_write_and_traffic_figures():
     if per_pair is not None:          # the kernel sources still match the profiled ones
         assert per_pair >= 2.0 and bench.traffic_per_launch(10) == per_pair * 10
         assert tw["dram_bytes_per_pair"] >= 2.0
+
+
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench
+
+
+def test_cpu_baseline_leg_checks_what_it_is_given():
+    """The bench's oracle leg: timing figures, and the spot check it runs on the GPU's
+    values (here the oracle's own values, then one planted error)."""
+    import oracle
+    from oracle import threshold as oth
+    bench = _bench()
+    rs = synth.workload_plain_small()
+    n = rs.n
+
+    def exact(i, j):
+        return oracle.pairs(rs, i, j)
+
+    def one_wrong(i, j):
+        d = oracle.pairs(rs, i, j).copy()
+        d[0] ^= 1
+        return d
+
+    for fn, want in ((exact, 0), (one_wrong, 1)):
+        out = bench.cpu_oracle_sample(rs, 0.05, gpu_pairs=fn)
+        assert out["kind"] == "oracle" and out["value"] > 0 and out["check"]["mismatches"] == want
+
+    i = np.arange(0, 40)
+    j = np.arange(1, 41)
+    got = oracle.pairs(rs, i, j)
+    assert bench.cpu_baseline_pairs(rs, i, j, got=got)["check"]["mismatches"] == 0
+    got[3] += 1
+    assert bench.cpu_baseline_pairs(rs, i, j, got=got)["check"]["mismatches"] == 1
+
+    th = type("T", (), {"num": 6, "den": 100, "abs_max": 65535})()
+    tri = oracle.all_pairs(rs)
+    labels = oth.components(n, oth.threshold_edges(tri, rs.lengths, 6, 100))
+    iu, ju = np.triu_indices(n, 1)
+    c = bench.cpu_baseline_components(rs, iu[:500], ju[:500], th, labels)["check"]
+    assert c["hit_pairs_split"] == 0 and c["labels_are_roots"]
+    bad = labels.copy()
+    bad[bad == 0] = 1                 # read 0 loses its root
+    assert not bench.cpu_baseline_components(rs, iu[:50], ju[:50], th, bad)["check"]["labels_are_roots"]
+
+    ref = rs.subset(range(20, 150))
+    ref_lab = (np.arange(ref.n) % 3).astype(np.int32)
+    qs = rs.subset(range(0, 20))
+    D = oracle.rect(qs, 0, qs.n, ref, 0, ref.n)
+    want_rows = oth.annotate(D, qs.lengths, ref.lengths, ref_lab, 6, 100)
+    a = bench.cpu_baseline_annotate(qs, ref, ref_lab, th, want_rows)
+    assert a["check"] == {"rows_checked": 20, "mismatches": 0}
+
+
+def test_cpu_baseline_mds_runs_on_a_small_sample():
+    out = _bench().cpu_baseline_mds(1000, 16, 4, 1, n_sample=200)
+    assert out["kind"] == "oracle" and out["unit"] == "s" and out["value"] > 0
