@@ -6,8 +6,9 @@ imports nothing from the library.
 
 It wraps two plain C files, compiled with gcc on first use (or by `build()`):
   * sw_oracle.c -- Smith-Waterman local score from the full DP matrix, the distance
-    d = max(la, lb) - S, and threaded all-pairs / pair-list / rectangle drivers
-    (paper section 2.2);
+    d = max(la, lb) - S (or one of the other score-to-distance readings: min(la, lb) - S,
+    the raw score, or the normalised 1 - S/max(la, lb) on a 16-bit scale), and threaded
+    all-pairs / pair-list / rectangle drivers (paper section 2.2);
   * brute.c     -- the local score by listing every alignment of every pair of
     substrings, with no DP table, used to pin sw_oracle.c on tiny reads.
 Default scores: match +1, mismatch -1, linear gap -1 (the paper states none); an
@@ -31,6 +32,8 @@ _lock = threading.Lock()
 _lib = None
 
 MATCH, MISMATCH, GAP = 1, -1, 1
+# score-to-distance rules (the `conversion` argument of sw_oracle.c)
+CONV_MAX, CONV_MIN, CONV_SCORE, CONV_NORM = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -66,14 +69,16 @@ def _load():
             lib.oracle_tri_index.restype = ctypes.c_uint64
             lib.oracle_sw_score_affine.argtypes = [u8p, i64, u8p, i64, ci, ci, ci, ci]
             lib.oracle_sw_score_affine.restype = ci
-            lib.oracle_all_pairs.argtypes = [u8p, u64p, ctypes.c_uint64, u16p, ci, ci, ci, ci, ci]
+            lib.oracle_distance_conv.argtypes = [u8p, i64, u8p, i64, ci, ci, ci, ci, ci]
+            lib.oracle_distance_conv.restype = ci
+            lib.oracle_all_pairs.argtypes = [u8p, u64p, ctypes.c_uint64, u16p, ci, ci, ci, ci, ci, ci]
             lib.oracle_pairs.argtypes = [u8p, u64p, u8p, u64p, u64p, u64p, ctypes.c_uint64, u16p,
-                                         ci, ci, ci, ci, ci]
+                                         ci, ci, ci, ci, ci, ci]
             lib.oracle_pair_scores.argtypes = [u8p, u64p, u8p, u64p, u64p, u64p, ctypes.c_uint64,
                                                ctypes.POINTER(ctypes.c_int32), ci, ci, ci, ci, ci]
             lib.oracle_rect.argtypes = [u8p, u64p, ctypes.c_uint64, ctypes.c_uint64, u8p, u64p,
                                         ctypes.c_uint64, ctypes.c_uint64, u16p, ctypes.c_uint64,
-                                        ci, ci, ci, ci, ci]
+                                        ci, ci, ci, ci, ci, ci]
             lib.brute_local_score.argtypes = [u8p, ci, u8p, ci, ci, ci, ci]
             lib.brute_local_score.restype = ci
             lib.brute_local_score_affine.argtypes = [u8p, ci, u8p, ci, ci, ci, ci, ci]
@@ -114,6 +119,13 @@ def distance(a, b, match=MATCH, mismatch=MISMATCH, gap=GAP) -> int:
                                    len(b), match, mismatch, gap)
 
 
+def distance_conv(a, b, conversion, match=MATCH, mismatch=MISMATCH, gap=GAP, gap_open=0) -> int:
+    """Distance of two reads under a conversion rule (CONV_*), linear or affine gaps."""
+    A, B = _bytes(a), _bytes(b)
+    return _load().oracle_distance_conv(_ptr(A, ctypes.c_uint8), len(a), _ptr(B, ctypes.c_uint8),
+                                        len(b), match, mismatch, gap, gap_open, conversion)
+
+
 def tri_index(i: int, j: int, n: int) -> int:
     return _load().oracle_tri_index(i, j, n)
 
@@ -125,19 +137,20 @@ def _seq_off(rs):
     return seq, np.ascontiguousarray(rs.offsets, dtype=np.uint64)
 
 
-def all_pairs(rs, match=MATCH, mismatch=MISMATCH, gap=GAP, nthreads=None, gap_open=0) -> np.ndarray:
+def all_pairs(rs, match=MATCH, mismatch=MISMATCH, gap=GAP, nthreads=None, gap_open=0,
+              conversion=CONV_MAX) -> np.ndarray:
     """Strict upper triangle (row-major, uint16) of all pairwise distances of a ReadSet."""
     n = rs.n
     out = np.zeros(max(n * (n - 1) // 2, 1), dtype=np.uint16)
     seq, off = _seq_off(rs)
     _load().oracle_all_pairs(_ptr(seq, ctypes.c_uint8), _ptr(off, ctypes.c_uint64), n,
                              _ptr(out, ctypes.c_uint16), match, mismatch, gap, gap_open,
-                             _threads(nthreads))
+                             conversion, _threads(nthreads))
     return out[: n * (n - 1) // 2]
 
 
 def pairs(rsA, pi, pj, rsB=None, match=MATCH, mismatch=MISMATCH, gap=GAP,
-          nthreads=None, gap_open=0) -> np.ndarray:
+          nthreads=None, gap_open=0, conversion=CONV_MAX) -> np.ndarray:
     """out[p] = d(A[pi[p]], B[pj[p]]) (B defaults to A)."""
     rsB = rsA if rsB is None else rsB
     pi = np.ascontiguousarray(pi, dtype=np.uint64)
@@ -149,7 +162,7 @@ def pairs(rsA, pi, pj, rsB=None, match=MATCH, mismatch=MISMATCH, gap=GAP,
                          _ptr(sb, ctypes.c_uint8), _ptr(ob, ctypes.c_uint64),
                          _ptr(pi, ctypes.c_uint64), _ptr(pj, ctypes.c_uint64), len(pi),
                          _ptr(out, ctypes.c_uint16), match, mismatch, gap, gap_open,
-                         _threads(nthreads))
+                         conversion, _threads(nthreads))
     return out[: len(pi)]
 
 
@@ -171,7 +184,7 @@ def pair_scores(rsA, pi, pj, rsB=None, match=MATCH, mismatch=MISMATCH, gap=GAP,
 
 
 def rect(rsA, a0, a1, rsB, b0, b1, match=MATCH, mismatch=MISMATCH, gap=GAP,
-         nthreads=None, gap_open=0) -> np.ndarray:
+         nthreads=None, gap_open=0, conversion=CONV_MAX) -> np.ndarray:
     """Row-major (a1-a0) x (b1-b0) block of distances d(A[r], B[c])."""
     ld = b1 - b0
     out = np.zeros(max((a1 - a0) * ld, 1), dtype=np.uint16)
@@ -180,7 +193,7 @@ def rect(rsA, a0, a1, rsB, b0, b1, match=MATCH, mismatch=MISMATCH, gap=GAP,
     _load().oracle_rect(_ptr(sa, ctypes.c_uint8), _ptr(oa, ctypes.c_uint64), a0, a1,
                         _ptr(sb, ctypes.c_uint8), _ptr(ob, ctypes.c_uint64), b0, b1,
                         _ptr(out, ctypes.c_uint16), ld, match, mismatch, gap, gap_open,
-                        _threads(nthreads))
+                        conversion, _threads(nthreads))
     return out[: (a1 - a0) * ld].reshape(a1 - a0, ld)
 
 

@@ -19,7 +19,16 @@
  *                 H(i,j) = max(0, H(i-1,j-1) + s(a_i,b_j), H(i-1,j) - g, H(i,j-1) - g),
  *                 S = max over all cells of H   (Smith & Waterman 1981, textbook form)
  *   distance      d = max(la, lb) - S           (stored as an unsigned 16-bit integer,
- *                                                 clamped into [0, 65535])
+ *                                                 clamped into [0, 65535]); the paper leaves
+ *                 the score-to-distance rule open (the authors' own note in section 2.2
+ *                 asks whether the dissimilarity is a distance), so three other readings
+ *                 are selectable (argument `conversion`):
+ *                   1  d = min(la, lb) - S, clamped likewise (0 when one read lies inside
+ *                      the other, so not a metric);
+ *                   2  the raw score S, clamped likewise;
+ *                   3  normalised: d = floor(65535 * (m - S) / m) with m = max(la, lb) and
+ *                      m - S clamped into [0, m], i.e. 1 - S/m on a 16-bit fixed-point
+ *                      scale; d = 0 when both reads are empty.
  *   all pairs     strict upper triangle, row-major: k(i,j) = i*n - i*(i+1)/2 + (j-i-1)
  *
  * The implementation is the plain definition: the full (la+1) x (lb+1) matrix is
@@ -110,20 +119,36 @@ static int score_of(const uint8_t *a, int64_t la, const uint8_t *b, int64_t lb, 
  * score above 1 can make S exceed max(la, lb), and d is then 0. */
 static int clamp_u16(int64_t d) { return d < 0 ? 0 : (d > 65535 ? 65535 : (int)d); }
 
+/* The score-to-distance rules (conversion codes of the header comment). */
+static int convert_score(int64_t S, int64_t la, int64_t lb, int conversion)
+{
+    int64_t hi = la > lb ? la : lb;
+    int64_t lo = la < lb ? la : lb;
+    if (conversion == 1) return clamp_u16(lo - S);
+    if (conversion == 2) return clamp_u16(S);
+    if (conversion == 3) {
+        if (hi == 0) return 0;
+        int64_t x = hi - S;
+        if (x < 0) x = 0;
+        if (x > hi) x = hi;
+        return (int)((65535 * x) / hi);
+    }
+    return clamp_u16(hi - S);
+}
+
 int oracle_distance(const uint8_t *a, int64_t la, const uint8_t *b, int64_t lb,
                     int match, int mismatch, int gap)
 {
     int S = oracle_sw_score(a, la, b, lb, match, mismatch, gap);
-    int64_t m = la > lb ? la : lb;
-    return clamp_u16(m - S);
+    return convert_score(S, la, lb, 0);
 }
 
-static int distance_of(const uint8_t *a, int64_t la, const uint8_t *b, int64_t lb, int match, int mismatch,
-                       int gap_open, int gap)
+/* Distance under any conversion rule, linear or affine gaps. */
+int oracle_distance_conv(const uint8_t *a, int64_t la, const uint8_t *b, int64_t lb, int match,
+                         int mismatch, int gap, int gap_open, int conversion)
 {
     int S = score_of(a, la, b, lb, match, mismatch, gap_open, gap);
-    int64_t m = la > lb ? la : lb;
-    return clamp_u16(m - S);
+    return convert_score(S, la, lb, conversion);
 }
 
 /* Position of pair (i, j), i < j, in the row-major strict upper triangle of n reads. */
@@ -146,6 +171,7 @@ typedef struct {
     uint16_t *out;
     int32_t *out_score;       /* pairs mode: raw scores S instead of distances */
     int match, mismatch, gap, gap_open;
+    int conversion;           /* score-to-distance rule (0 = max(la, lb) - S) */
     int mode;                 /* 0 = triangle rows, 1 = pair list, 2 = rectangle rows */
     uint64_t next;            /* shared work counter */
 } job_t;
@@ -167,8 +193,8 @@ static void *worker(void *arg)
             for (uint64_t j = i + 1; j < J->n; ++j) {
                 const uint8_t *b = J->seq + J->off[j];
                 int64_t lb = (int64_t)(J->off[j + 1] - J->off[j]);
-                J->out[oracle_tri_index(i, j, J->n)] =
-                    (uint16_t)distance_of(a, la, b, lb, J->match, J->mismatch, J->gap_open, J->gap);
+                J->out[oracle_tri_index(i, j, J->n)] = (uint16_t)oracle_distance_conv(
+                    a, la, b, lb, J->match, J->mismatch, J->gap, J->gap_open, J->conversion);
             }
         }
     } else if (J->mode == 1) {
@@ -185,8 +211,8 @@ static void *worker(void *arg)
                 if (J->out_score)
                     J->out_score[p] = score_of(a, la, b, lb, J->match, J->mismatch, J->gap_open, J->gap);
                 else
-                    J->out[p] = (uint16_t)distance_of(a, la, b, lb, J->match, J->mismatch, J->gap_open,
-                                                      J->gap);
+                    J->out[p] = (uint16_t)oracle_distance_conv(a, la, b, lb, J->match, J->mismatch, J->gap,
+                                                               J->gap_open, J->conversion);
             }
         }
     } else {
@@ -198,8 +224,8 @@ static void *worker(void *arg)
             for (uint64_t c = J->b0; c < J->b1; ++c) {
                 const uint8_t *b = J->seqB + J->offB[c];
                 int64_t lb = (int64_t)(J->offB[c + 1] - J->offB[c]);
-                J->out[(r - J->a0) * J->ld + (c - J->b0)] =
-                    (uint16_t)distance_of(a, la, b, lb, J->match, J->mismatch, J->gap_open, J->gap);
+                J->out[(r - J->a0) * J->ld + (c - J->b0)] = (uint16_t)oracle_distance_conv(
+                    a, la, b, lb, J->match, J->mismatch, J->gap, J->gap_open, J->conversion);
             }
         }
     }
@@ -224,25 +250,28 @@ static int run(job_t *J, int nthreads)
 
 /* All pairs i < j of one read set into the strict upper triangle out[n(n-1)/2]. */
 int oracle_all_pairs(const uint8_t *seq, const uint64_t *off, uint64_t n, uint16_t *out,
-                     int match, int mismatch, int gap, int gap_open, int nthreads)
+                     int match, int mismatch, int gap, int gap_open, int conversion, int nthreads)
 {
     job_t J;
     memset(&J, 0, sizeof J);
     J.seq = seq; J.off = off; J.n = n; J.out = out;
     J.match = match; J.mismatch = mismatch; J.gap = gap; J.gap_open = gap_open; J.mode = 0;
+    J.conversion = conversion;
     return run(&J, nthreads);
 }
 
-/* Listed pairs: out[p] = d(A[pi[p]], B[pj[p]]). */
+/* Listed pairs: out[p] = d(A[pi[p]], B[pj[p]]) under the given conversion rule. */
 int oracle_pairs(const uint8_t *seqA, const uint64_t *offA, const uint8_t *seqB,
                  const uint64_t *offB, const uint64_t *pi, const uint64_t *pj, uint64_t npairs,
-                 uint16_t *out, int match, int mismatch, int gap, int gap_open, int nthreads)
+                 uint16_t *out, int match, int mismatch, int gap, int gap_open, int conversion,
+                 int nthreads)
 {
     job_t J;
     memset(&J, 0, sizeof J);
     J.seq = seqA; J.off = offA; J.seqB = seqB; J.offB = offB;
     J.pi = pi; J.pj = pj; J.npairs = npairs; J.out = out;
     J.match = match; J.mismatch = mismatch; J.gap = gap; J.gap_open = gap_open; J.mode = 1;
+    J.conversion = conversion;
     return run(&J, nthreads);
 }
 
@@ -264,12 +293,13 @@ int oracle_pair_scores(const uint8_t *seqA, const uint64_t *offA, const uint8_t 
 int oracle_rect(const uint8_t *seqA, const uint64_t *offA, uint64_t a0, uint64_t a1,
                 const uint8_t *seqB, const uint64_t *offB, uint64_t b0, uint64_t b1,
                 uint16_t *out, uint64_t ld, int match, int mismatch, int gap, int gap_open,
-                int nthreads)
+                int conversion, int nthreads)
 {
     job_t J;
     memset(&J, 0, sizeof J);
     J.seq = seqA; J.off = offA; J.seqB = seqB; J.offB = offB;
     J.a0 = a0; J.a1 = a1; J.b0 = b0; J.b1 = b1; J.ld = ld; J.out = out;
     J.match = match; J.mismatch = mismatch; J.gap = gap; J.gap_open = gap_open; J.mode = 2;
+    J.conversion = conversion;
     return run(&J, nthreads);
 }

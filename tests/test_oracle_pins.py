@@ -9,7 +9,10 @@ distance d = max(la, lb) - S (paper section 2.2).  It is checked here against
   * invariants: d(x,x) = 0, symmetry, |la - lb| <= d <= max(la, lb),
   * closed forms: a read inside another gives S = |x|; S is at least the best
     gap-free diagonal segment (a maximum-subarray problem, solved by Kadane's scan),
-  * the strict upper-triangle layout of ~n^2/2 values for n reads (section 2.2).
+  * the strict upper-triangle layout of ~n^2/2 values for n reads (section 2.2),
+  * the other score-to-distance readings (min length minus S, the raw score, the
+    normalised 1 - S/max): hand-worked values (tests/golden/conversions.txt) and the
+    relations between the readings that the definitions fix.
 """
 import os
 
@@ -240,3 +243,95 @@ def test_distance_clamped_into_uint16_range():
     tri = oracle.all_pairs(rs, match=2, mismatch=-3, gap=1)
     assert tri.tolist() == [0, 2, 2]                  # S = 16, 6, 6 against max = 8, 8, 8
     assert oracle.all_pairs(rs).tolist() == [0, 5, 5]
+
+
+# ------------------------------------------------------------------ conversions
+
+CONV_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "conversions.txt")
+
+
+def _conv_cases():
+    rows = []
+    with open(CONV_GOLDEN) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            a, b, S, dmax, dmin, dnorm = line.split()
+            rows.append(("" if a == "-" else a, "" if b == "-" else b, int(S), int(dmax), int(dmin), int(dnorm)))
+    return rows
+
+
+CONV = _conv_cases()
+
+
+def test_conversion_cases_loaded():
+    assert len(CONV) >= 12
+
+
+@pytest.mark.parametrize("a,b,S,dmax,dmin,dnorm", CONV)
+def test_conversion_hand_cases(a, b, S, dmax, dmin, dnorm):
+    for x, y in ((a, b), (b, a)):
+        assert oracle.sw_score(x, y) == S
+        assert oracle.distance_conv(x, y, oracle.CONV_MAX) == dmax
+        assert oracle.distance_conv(x, y, oracle.CONV_MIN) == dmin
+        assert oracle.distance_conv(x, y, oracle.CONV_SCORE) == S
+        assert oracle.distance_conv(x, y, oracle.CONV_NORM) == dnorm
+
+
+def test_conversion_clamps_hand_cases():
+    """With match +3 the score can exceed both lengths: every length-based reading clamps
+    at 0 (worked by hand: AC vs AC scores 6; A vs AC scores 3)."""
+    for a, b, S in (("AC", "AC", 6), ("A", "AC", 3)):
+        for conv, want in ((oracle.CONV_MAX, 0), (oracle.CONV_MIN, 0), (oracle.CONV_NORM, 0),
+                           (oracle.CONV_SCORE, S)):
+            assert oracle.distance_conv(a, b, conv, match=3, mismatch=-1, gap=1) == want
+
+
+def test_conversion_relations_exhaustive_len4():
+    """Every pair of reads of length <= 4 (default scores; the score S from the brute force,
+    which shares nothing with the DP):
+      * dmax - dmin = |la - lb| (both subtract the same S);
+      * dmin = 0 exactly when the shorter read occurs in the longer one gap-free;
+      * dnorm = 0 exactly when dmax = 0, dnorm = 65535 exactly when S = 0 and a read is
+        non-empty, and dnorm is non-decreasing in dmax among pairs of one longer length;
+      * the raw-score reading equals the brute-force score."""
+    strings = oracle.brute_strings(4)
+    brute = oracle.brute_exhaustive(4)
+    rs = synth.from_strings([s.decode() for s in strings])
+    n = len(strings)
+    pi, pj = (x.ravel() for x in np.meshgrid(np.arange(n), np.arange(n), indexing="ij"))
+    got = {c: oracle.pairs(rs, pi, pj, conversion=c).astype(np.int64)
+           for c in (oracle.CONV_MAX, oracle.CONV_MIN, oracle.CONV_SCORE, oracle.CONV_NORM)}
+    L = np.array([len(s) for s in strings])
+    la, lb = L[pi], L[pj]
+    S = brute.ravel()
+    np.testing.assert_array_equal(got[oracle.CONV_SCORE], S)
+    np.testing.assert_array_equal(got[oracle.CONV_MAX] - got[oracle.CONV_MIN], np.abs(la - lb))
+    inside = np.array([(strings[x] in strings[y]) if len(strings[x]) <= len(strings[y]) else (strings[y] in strings[x])
+                       for x, y in zip(pi, pj)])
+    np.testing.assert_array_equal(got[oracle.CONV_MIN] == 0, inside)
+    dn, dm = got[oracle.CONV_NORM], got[oracle.CONV_MAX]
+    np.testing.assert_array_equal(dn == 0, dm == 0)
+    nonempty = np.maximum(la, lb) > 0
+    np.testing.assert_array_equal(dn == 65535, (S == 0) & nonempty)
+    m = np.maximum(la, lb)
+    for mv in range(1, 5):
+        sel = m == mv
+        order = np.argsort(dm[sel], kind="stable")
+        assert np.all(np.diff(dn[sel][order]) >= 0)
+
+
+@pytest.mark.parametrize("go", [0, 3])
+def test_conversion_drivers_agree(go):
+    """The triangle, pair-list and rectangle drivers apply the same rule as the single-pair
+    function, for every reading, with linear and affine gaps."""
+    rs = synth.workload_plain_small().subset(range(12))
+    n = rs.n
+    pi, pj = np.triu_indices(n, 1)
+    for conv in (oracle.CONV_MAX, oracle.CONV_MIN, oracle.CONV_SCORE, oracle.CONV_NORM):
+        one = np.array([oracle.distance_conv(rs.read(i), rs.read(j), conv, gap_open=go) for i, j in zip(pi, pj)])
+        np.testing.assert_array_equal(oracle.all_pairs(rs, gap_open=go, conversion=conv), one)
+        np.testing.assert_array_equal(oracle.pairs(rs, pi, pj, gap_open=go, conversion=conv), one)
+        R = oracle.rect(rs, 0, n, rs, 0, n, gap_open=go, conversion=conv)
+        np.testing.assert_array_equal(R[pi, pj], one)
