@@ -449,7 +449,7 @@ int gbd_create(gbd_ctx **out, int device, const gbd_params *p)
     if (p) prm = *p;
     if (prm.gap < 0) return fail(GBD_EINVAL, "gbd_create: gap penalty must be >= 0");
     if (prm.gap_open < 0) return fail(GBD_EINVAL, "gbd_create: gap opening penalty must be >= 0");
-    if (prm.conversion < GBD_CONV_MAX || prm.conversion > GBD_CONV_SCORE)
+    if (prm.conversion < GBD_CONV_MAX || prm.conversion > GBD_CONV_NORM)
         return fail(GBD_EINVAL, "gbd_create: unknown conversion");
     if (prm.kernel < GBD_KERNEL_AUTO || prm.kernel > GBD_KERNEL_SYSTOLIC)
         return fail(GBD_EINVAL, "gbd_create: unknown kernel choice");

@@ -26,6 +26,25 @@ int cuda_fail(cudaError_t e, const char *what);
 // Count of kernel launches made by the library (see gbd_kernel_launches).
 void note_launches(uint64_t k);
 
+// Score-to-distance rule (GBD_CONV_*) applied to the local score S of reads of lengths
+// la and lb; the result is stored as uint16.  GBD_CONV_NORM divides in 32 bits: 65535 * x
+// with x <= m <= 65535 stays below 2^32.
+__device__ __forceinline__ uint16_t score_to_distance(int S, int la, int lb, int conversion)
+{
+    const int hi = max(la, lb);
+    if (conversion == GBD_CONV_NORM) {
+        if (hi == 0) return 0;
+        const int x = min(max(hi - S, 0), hi);
+        return (uint16_t)((65535u * (uint32_t)x) / (uint32_t)hi);
+    }
+    int d;
+    if (conversion == GBD_CONV_SCORE) d = S;
+    else if (conversion == GBD_CONV_MIN) d = min(la, lb) - S;
+    else d = hi - S;
+    d = d < 0 ? 0 : (d > 65535 ? 65535 : d);
+    return (uint16_t)d;
+}
+
 // ------------------------------------------------------------------ packed read sets
 constexpr int kBasesPerWord = 16;
 

@@ -46,16 +46,6 @@ __device__ __forceinline__ void tri_unindex(uint64_t k, uint64_t n, uint64_t &i,
     j = k - tri_row_start(i, n) + i + 1;
 }
 
-__device__ __forceinline__ uint16_t convert(int S, int la, int lb, int conversion)
-{
-    int d;
-    if (conversion == GBD_CONV_SCORE) d = S;
-    else if (conversion == GBD_CONV_MIN) d = min(la, lb) - S;
-    else d = max(la, lb) - S;
-    d = d < 0 ? 0 : (d > 65535 ? 65535 : d);
-    return (uint16_t)d;
-}
-
 // Linear gaps: H = max(0, H_d + s, H_u - gap, H_l - gap).  Affine gaps (Gotoh): E carries
 // a horizontal gap run along the strip's rows, F a vertical one down the column (across
 // strips through a second boundary row), H = max(0, H_d + s, E, F) with
@@ -137,7 +127,7 @@ sw_general_kernel(GeneralJob job, Scoring sc, int *__restrict__ scratch, uint64_
                 if (AFFINE) bndf[(uint64_t)j * nthr] = fup;
             }
         }
-        job.out[o] = convert(best, la, lb, sc.conversion);
+        job.out[o] = score_to_distance(best, la, lb, sc.conversion);
     }
 }
 

@@ -94,16 +94,6 @@ __device__ __forceinline__ uint32_t lop_sel(uint32_t keep, uint32_t repl, uint32
     return (keep & ~mask) | (repl & mask);
 }
 
-__device__ __forceinline__ uint16_t convert_d(int S, int la, int lb, int conversion)
-{
-    int d;
-    if (conversion == GBD_CONV_SCORE) d = S;
-    else if (conversion == GBD_CONV_MIN) d = min(la, lb) - S;
-    else d = max(la, lb) - S;
-    d = d < 0 ? 0 : (d > 65535 ? 65535 : d);
-    return (uint16_t)d;
-}
-
 // One warp's work: a piece of an entry.
 struct SysUnit {
     uint32_t job, q, sub_begin, nsub;
@@ -433,7 +423,7 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
                         } else {
                             idx = ((uint64_t)u.q - J.row0) * J.ld + ((uint64_t)so - J.col0);
                         }
-                        J.out[idx] = convert_d(S, la, lb, conv);
+                        J.out[idx] = score_to_distance(S, la, lb, conv);
                     }
                 }
             }

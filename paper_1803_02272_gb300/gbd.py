@@ -19,7 +19,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libgbd.so")
 
 GBD_OK, GBD_EINVAL, GBD_ENOMEM, GBD_EBUDGET, GBD_ETIMEDOUT, GBD_ECUDA, GBD_ENOTFOUND = range(7)
-GBD_CONV_MAX, GBD_CONV_MIN, GBD_CONV_SCORE = 0, 1, 2
+GBD_CONV_MAX, GBD_CONV_MIN, GBD_CONV_SCORE, GBD_CONV_NORM = 0, 1, 2, 3
 GBD_KERNEL_AUTO, GBD_KERNEL_GENERAL, GBD_KERNEL_SYSTOLIC = 0, 1, 2
 PROBE_OPS = ["VIMAX3_S16X2_RELU", "VIADDMAX_S16X2", "VIADDMAX_S16X2_RELU", "VIMAX_S16X2_RELU",
              "VMAXS2", "PRMT", "IADD3", "LOP3", "IMAX", "HMAX2", "HADD2", "CELL_MIX",

@@ -320,11 +320,19 @@ def test_systolic_rejects_other_scores(gbd):
     assert ei.value.code == gbd.GBD_EINVAL
 
 
+def _tile_pairs(n, r0, r1, c0, c1):
+    """Every pair (i, j), i < j, of the block rows [r0, r1) x columns [c0, c1)."""
+    ii, jj = np.meshgrid(np.arange(r0, r1), np.arange(c0, c1), indexing="ij")
+    keep = ii < jj
+    return ii[keep].astype(np.int64), jj[keep].astype(np.int64)
+
+
 def test_paper_scale_sampled(gbd):
     """The paper-scale workload (10^5 reads, 5.0e9 pairs, the 10 GB triangle) in the launch
-    configuration the benchmark times: 20,000 seeded pairs and the whole rows of three
-    reads (first, middle, the longest) checked against the oracle; d(x, x) = 0 and the
-    length bounds hold on every sampled pair."""
+    configuration the benchmark times: 20,000 seeded pairs, the whole rows of three reads
+    (first, middle, the longest) and four whole 64 x 1024 tiles of the triangle (the first,
+    the last, one in the middle and the one of the longest read) checked against the
+    oracle; the length bounds hold on every sampled pair."""
     import torch
     rs = synth.workload_paper_scale()
     n = rs.n
@@ -341,9 +349,81 @@ def test_paper_scale_sampled(gbd):
     np.testing.assert_array_equal(got, want)
     L = rs.lengths.astype(np.int64)
     assert np.all(got >= np.abs(L[i] - L[j])) and np.all(got <= np.maximum(L[i], L[j]))
-    for r in (0, n // 2, int(np.argmax(L[:-1]))):
+    longest = int(np.argmax(L[:-1]))
+    for r in (0, n // 2, longest):
         k0 = r * n - r * (r + 1) // 2
         row = gbd.as_uint16(tri[k0:k0 + (n - 1 - r)])
         jj = np.arange(r + 1, n)
         np.testing.assert_array_equal(row, oracle.pairs(rs, np.full(len(jj), r), jj))
+    lr = min(max(longest - 32, 0), n - 64)
+    tiles = {"first": (0, 64, 1, 1025), "last": (n - 64, n, n - 1024, n),
+             "middle": (n // 2, n // 2 + 64, n // 2 + 1, n // 2 + 1025),
+             "longest read": (lr, lr + 64, lr + 1, min(lr + 1025, n))}
+    for name, (r0, r1, c0, c1) in tiles.items():
+        ti, tj = _tile_pairs(n, r0, r1, c0, c1)
+        idx = ti * n - ti * (ti + 1) // 2 + (tj - ti - 1)
+        got = gbd.as_uint16(tri[torch.from_numpy(idx).cuda()])
+        np.testing.assert_array_equal(got, oracle.pairs(rs, ti, tj), err_msg=f"{name} tile")
     del tri
+
+
+# ------------------------------------------------------------------ score-to-distance rules
+# Section 2.2 leaves the conversion of the local score into a dissimilarity open; every
+# reading behind gbd_params.conversion is compared with the oracle's mode of the same rule.
+
+CONVERSIONS = ["min", "norm", "score"]
+
+
+def _conv_codes(gbd, name):
+    return {"max": (gbd.GBD_CONV_MAX, oracle.CONV_MAX), "min": (gbd.GBD_CONV_MIN, oracle.CONV_MIN),
+            "score": (gbd.GBD_CONV_SCORE, oracle.CONV_SCORE), "norm": (gbd.GBD_CONV_NORM, oracle.CONV_NORM)}[name]
+
+
+@pytest.mark.parametrize("conv", CONVERSIONS)
+@pytest.mark.parametrize("kernel", ["systolic", "general"])
+def test_conversions_all_pairs_exact(gbd, kernel, conv):
+    """Each conversion on each kernel: the 150-read workload (all 11,175 pairs) and the
+    edge-length reads (empty reads, a read inside another, lengths around every word and
+    lane boundary and past 512), bit-exact."""
+    cg, co = _conv_codes(gbd, conv)
+    ctx = _ctx(gbd, kernel, conversion=cg)
+    for rs in (synth.workload_plain_small(), synth.from_strings(_edge_reads())):
+        got = _all_pairs(gbd, ctx, rs)
+        np.testing.assert_array_equal(got, oracle.all_pairs(rs, conversion=co))
+
+
+@pytest.mark.parametrize("conv", CONVERSIONS)
+def test_conversions_affine_exact(gbd, conv):
+    """The conversions with affine gaps: on the systolic kernel (open 2 and 9, extend 1)
+    and on the general kernel (match 2, mismatch -3, extend 1, open 3)."""
+    cg, co = _conv_codes(gbd, conv)
+    rs = synth.workload_plain_small().subset(range(90))
+    edge = synth.from_strings(_edge_reads()[:30])
+    for go in (2, 9):
+        ctx = _ctx(gbd, "systolic", gap_open=go, conversion=cg)
+        for r in (rs, edge):
+            np.testing.assert_array_equal(_all_pairs(gbd, ctx, r), oracle.all_pairs(r, gap_open=go, conversion=co))
+    ctx = _ctx(gbd, "auto", match=2, mismatch=-3, gap=1, gap_open=3, conversion=cg)
+    for r in (rs, edge):
+        np.testing.assert_array_equal(_all_pairs(gbd, ctx, r),
+                                      oracle.all_pairs(r, match=2, mismatch=-3, gap=1, gap_open=3, conversion=co))
+
+
+@pytest.mark.parametrize("conv", CONVERSIONS)
+def test_conversions_tile_and_batch_exact(gbd, conv):
+    """The conversions through a rectangle (both kernels) and the batched launch."""
+    import torch
+    cg, co = _conv_codes(gbd, conv)
+    rs = synth.workload_plain_10k(n=260)
+    A, B = rs.subset(range(0, 100)), rs.subset(range(100, 260))
+    for kernel in ("auto", "general"):
+        ctx = _ctx(gbd, kernel, conversion=cg)
+        out = ctx.tile(ctx.load(A), 3, 97, ctx.load(B), 0, B.n)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(gbd.as_uint16(out), oracle.rect(A, 3, 97, B, 0, B.n, conversion=co))
+    samples = synth.workload_batched(n_samples=4, n_lo=20, n_hi=120)
+    ctx = _ctx(gbd, "auto", conversion=cg)
+    outs = ctx.batch([ctx.load(x) for x in samples])
+    torch.cuda.synchronize()
+    for x, o in zip(samples, outs):
+        np.testing.assert_array_equal(gbd.as_uint16(o), oracle.all_pairs(x, conversion=co))

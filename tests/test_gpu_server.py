@@ -44,6 +44,23 @@ def test_single_request_matches_oracle(env):
     srv.close()
 
 
+@pytest.mark.parametrize("conv", ["min", "norm"])
+def test_server_conversions_match_oracle(env, conv):
+    """A server of a context with another score-to-distance rule returns that rule's rows."""
+    import torch
+    gbd, _, _, ref_rs = env
+    cg, co = {"min": (gbd.GBD_CONV_MIN, oracle.CONV_MIN), "norm": (gbd.GBD_CONV_NORM, oracle.CONV_NORM)}[conv]
+    ctx = gbd.Context(0, conversion=cg)
+    sub = ref_rs.subset(range(0, 600))
+    srv = gbd.Server(ctx, ctx.load(sub))
+    q = _queries(5, [7])[0]
+    t, out = srv.submit(q)
+    srv.wait(t)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(gbd.as_uint16(out), oracle.rect(q, 0, q.n, sub, 0, sub.n, conversion=co))
+    srv.close()
+
+
 def test_rows_identical_alone_and_mixed(env):
     """Each request's rows are byte-identical whether it runs alone or among others."""
     import torch
