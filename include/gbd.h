@@ -47,10 +47,13 @@ extern "C" {
 #define GBD_ECUDA     5   /* a CUDA runtime call failed (message has the CUDA error) */
 #define GBD_ENOTFOUND 6   /* unknown server ticket */
 
-/* score-to-distance rules (gbd_params.conversion) */
+/* score-to-distance rules (gbd_params.conversion).  Section 2.2 derives the dissimilarity
+ * from the local score and leaves the rule open; these are the readings offered. */
 #define GBD_CONV_MAX   0  /* d = max(la, lb) - S, clamped to [0, 65535]  (default) */
 #define GBD_CONV_MIN   1  /* d = min(la, lb) - S, clamped to [0, 65535] */
 #define GBD_CONV_SCORE 2  /* the raw local score S, clamped to [0, 65535] */
+#define GBD_CONV_NORM  3  /* 1 - S/max(la, lb) in 16-bit fixed point: floor(65535 * x / m) with
+                             m = max(la, lb) and x = m - S clamped into [0, m]; 0 when m = 0 */
 
 /* kernel choice (gbd_params.kernel) */
 #define GBD_KERNEL_AUTO     0  /* systolic kernel where it applies, else the general one */
@@ -78,13 +81,15 @@ typedef struct {
                              row (n - 1 entries) */
 } gbd_params;
 
-/* Fills *p with the defaults above. */
+/* Fills *p with the defaults above (library plumbing; the paper fixes none of these values). */
 void gbd_default_params(gbd_params *p);
 
-/* sizeof(gbd_params) as compiled into the library (for bindings that mirror the struct). */
+/* sizeof(gbd_params) as compiled into the library (for bindings that mirror the struct;
+ * no paper counterpart). */
 uint64_t gbd_params_size(void);
 
-/* Creates a context on CUDA device `device` (made current on the calling thread).
+/* Creates a context on CUDA device `device` (made current on the calling thread); library
+ * plumbing with no paper counterpart.
  * p == NULL selects the defaults.  EINVAL on a negative gap or bad enum values.  The
  * library's scratch is stream-ordered (cudaMallocAsync from the device's default pool);
  * gbd_create raises that pool's release threshold to 4 GiB if it is lower, so scratch is
@@ -92,12 +97,15 @@ uint64_t gbd_params_size(void);
 int gbd_create(gbd_ctx **out, int device, const gbd_params *p);
 void gbd_destroy(gbd_ctx *ctx);
 
-/* Frees what the context keeps between calls (the MDS square, the captured batch graph)
+/* (No paper counterpart.)  Frees what the context keeps between calls (the MDS square, the
+ * captured batch graph)
  * after waiting for the device to finish its work.  The next call that needs them
  * rebuilds them.  EINVAL on a NULL context. */
 int gbd_trim(gbd_ctx *ctx);
 
-/* Ingest (a1): copies (if host pointers) and packs n reads into a device-resident set:
+/* The input of the distance computation (section 2.2: `disseq` reads the sequences of its
+ * read files; the all-pairs run reads the ~1e5 amplicon reads of one sample, section 6.1).
+ * Copies (if host pointers) and packs n reads into a device-resident set:
  * 2-bit codes A=0 C=1 G=2 T=3, 16 bases per uint32 (base k of a word in bits 2k..2k+1),
  * a fixed stride of ceil(max_len/16) words per read, and per-read uint16 lengths.
  * `seq` and `offsets` (n+1 entries, offsets[0] may be non-zero) may both be host or both
@@ -111,23 +119,30 @@ uint32_t gbd_set_max_len(const gbd_set *set);        /* longest read */
 /* Sum over the pairs i < j of len_i * len_j: the DP cells of gbd_all_pairs. */
 double gbd_set_pair_cells(const gbd_set *set);
 
-/* All pairs (a2-a4): d_tri[k(i,j)] = d(read i, read j) for every i < j, with the
+/* All pairwise distances of one read set (section 2.2: the matrix D of all ~5e9 pairwise
+ * values of a ~1e5-read sample, every pair computed independently; one value per unordered
+ * pair, the distance being symmetric): d_tri[k(i,j)] = d(read i, read j) for every i < j, with the
  * row-major strict upper triangle index k(i,j) = i*n - i*(i+1)/2 + (j-i-1).
  * tri_len must equal n(n-1)/2 (EINVAL otherwise); d_tri is a device pointer. */
 int gbd_all_pairs(gbd_ctx *ctx, const gbd_set *set, uint16_t *d_tri, uint64_t tri_len,
                   void *stream);
 
-/* Rectangle (the m x n form of `disseq`): d_out[(r-a0)*ld + (c-b0)] = d(A[r], B[c])
+/* Rectangle (section 2.2: `disseq` on two read files of m and n reads returns the m x n
+ * matrix D with d_ij the distance between read i of the first and read j of the second):
+ * d_out[(r-a0)*ld + (c-b0)] = d(A[r], B[c])
  * for r in [a0,a1), c in [b0,b1); ld >= b1-b0.  A and B may be the same set. */
 int gbd_tile(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd_set *B,
              uint64_t b0, uint64_t b1, uint16_t *d_out, uint64_t ld, void *stream);
 
-/* Batched samples: one launch computes the all-pairs triangle of each of ns sets;
+/* Batched samples (section 6.1: ten Lake Geneva samples L_1..L_10 of 7e4 to 1.4e5 reads each,
+ * whose distances are computed sample by sample, section 2.2): one launch group computes the
+ * all-pairs triangle of each of ns sets;
  * d_tris[s] receives sample s's triangle (n_s(n_s-1)/2 entries, device pointers). */
 int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns,
               uint16_t *const *d_tris, void *stream);
 
-/* The batched launch tunes itself online: the first calls with a new list of samples and
+/* (No paper counterpart: the tuning of this library's batched launch.)  The batched launch
+ * tunes itself online: the first calls with a new list of samples and
  * outputs run the launch group with work units of 1, 0.5 and 2 times the cost model's size
  * (timed with events on `stream`; each of these calls first waits for the previous one to
  * finish), and from the fourth call on the fastest is replayed as a CUDA graph.  Results are
@@ -135,7 +150,10 @@ int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns,
  * measured), the scale in use and whether tuning has finished; ENOTFOUND before any batch. */
 int gbd_batch_tuning(const gbd_ctx *ctx, double *trial_ms, double *scale, int *done);
 
-/* Serving (a5): a resident reference set answers query batches with distance rows.
+/* Query rows against a resident reference set (section 4.3: the distances between every
+ * read of a sample and the ~2e3 annotated reads of a reference database, computed as a
+ * rectangle by `MPI-disseq`; the rows place new reads against known ones).  A server keeps
+ * the reference set resident and answers query batches with distance rows.
  * submit copies the queries (host pointers, nq reads) and returns at once with a
  * ticket; the request is admitted when its memory fits the budget beside the requests
  * in flight, and its work overlaps theirs on the device.  d_rows (device, nq x n_ref,
@@ -160,10 +178,12 @@ void gbd_server_destroy(gbd_server *srv);
  * every GPU loading the library holds until the process exits; inputs whose packed form
  * plus one thread block's boundary rows do not fit return GBD_EINVAL.  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress) and should come
- * before any stream capture.  All calls share the one array and the call synchronises
- * `stream` once to read its validation flags; calls that overlap on the GPU (other
+ * before any stream capture.  All calls share the one array; calls that overlap on the GPU (other
  * streams, other host threads) race on the array and must be serialised by the caller.
- * Errors: EINVAL for a non-ACGT byte, a read longer than max_len, decreasing offsets,
+ * The offsets are checked (one synchronisation of `stream`) before any kernel reads the
+ * bytes, and the bytes are checked (a second synchronisation) before any distance is
+ * computed.  Errors: EINVAL for a NULL pointer (d_seqA and d_seqB too, even when every
+ * read is empty), a non-ACGT byte, a read longer than max_len, decreasing offsets,
  * ld < nB, or inputs too large for the array. */
 int gbd_tile_noalloc(gbd_ctx *ctx, const uint8_t *d_seqA, const uint64_t *d_offA, uint64_t nA,
                      const uint8_t *d_seqB, const uint64_t *d_offB, uint64_t nB,
@@ -267,14 +287,16 @@ int gbd_gram_apply(gbd_ctx *ctx, const uint16_t *d_w, uint64_t n, uint64_t ld, i
 int gbd_mds(gbd_ctx *ctx, const uint16_t *d_tri, uint64_t n, const float *d_omega, uint32_t k,
             uint32_t r, uint32_t q, float *d_lambda, float *d_coords, void *stream);
 
-/* Thread-local text of the last error raised on the calling thread ("" if none). */
+/* Thread-local text of the last error raised on the calling thread ("" if none; no paper
+ * counterpart). */
 const char *gbd_last_error(void);
 
-/* Measurement support: number of CUDA kernels this library has launched in the
- * process so far (all contexts, all devices). */
+/* Measurement support (no paper counterpart): number of CUDA kernels this library has
+ * launched in the process so far (all contexts, all devices). */
 uint64_t gbd_kernel_launches(void);
 
-/* Measurement support: issue rate of one instruction form of the DP inner loop,
+/* Measurement support (no paper counterpart): issue rate of one instruction form of the
+ * DP inner loop,
  * in lane operations per second (op codes GBD_PROBE_*), timed with CUDA events
  * on `stream` over `iters` iterations of a saturating kernel. */
 #define GBD_PROBE_VIMAX3_S16X2_RELU  0
