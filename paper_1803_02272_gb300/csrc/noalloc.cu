@@ -69,17 +69,23 @@ extern "C" int gbd_tile_noalloc(gbd_ctx *ctx, const uint8_t *d_seqA, const uint6
 {
     if (!ctx) return fail(GBD_EINVAL, "gbd_tile_noalloc: NULL context");
     if (nA == 0 || nB == 0) return GBD_OK;
-    if (!d_offA || !d_offB || !d_out) return fail(GBD_EINVAL, "gbd_tile_noalloc: NULL pointer");
+    if (!d_seqA || !d_seqB || !d_offA || !d_offB || !d_out)
+        return fail(GBD_EINVAL, "gbd_tile_noalloc: NULL pointer");
     if (ld < nB) return fail(GBD_EINVAL, "gbd_tile_noalloc: ld is smaller than nB");
     if (max_len > 65535) return fail(GBD_EINVAL, "gbd_tile_noalloc: max_len above 65535");
+    // layout: 4 flags | A words | A lengths | B words | B lengths | boundary rows
+    const uint32_t stride = max_len == 0 ? 1u : (max_len + kBasesPerWord - 1) / kBasesPerWord;
+    // every read set alone must fit the array: this keeps the products below from wrapping
+    const uint64_t max_reads = kNoAllocScratchBytes / (4ull * stride);
+    if (nA > max_reads || nB > max_reads)
+        return fail(GBD_EINVAL, "gbd_tile_noalloc: more reads than the " + std::to_string(kNoAllocScratchBytes) +
+                                    "-byte scratch array of the allocation-free entry point holds");
     cudaStream_t st = (cudaStream_t)stream;
     GBD_CUDA_TRY(cudaSetDevice(ctx->device));
     unsigned char *base = nullptr;
     int rc = scratch_for_device(ctx->device, &base);
     if (rc != GBD_OK) return rc;
 
-    // layout: 4 flags | A words | A lengths | B words | B lengths | boundary rows
-    const uint32_t stride = max_len == 0 ? 1u : (max_len + kBasesPerWord - 1) / kBasesPerWord;
     const uint64_t off_wA = 256;
     const uint64_t off_lA = align256(off_wA + nA * stride * 4);
     const uint64_t off_wB = align256(off_lA + nA * 2);
@@ -103,21 +109,24 @@ extern "C" int gbd_tile_noalloc(gbd_ctx *ctx, const uint8_t *d_seqA, const uint6
     check_offsets_kernel<<<64, 256, 0, st>>>(d_offB, nB, max_len, flags + 1);
     note_launches(2);
     GBD_CUDA_TRY(cudaGetLastError());
-    GBD_CUDA_TRY(launch_pack(d_seqA, d_offA, nA, stride, wA, lA, flags + 2, st));
-    GBD_CUDA_TRY(launch_pack(d_seqB, d_offB, nB, stride, wB, lB, flags + 3, st));
+    // the offsets are read back and checked before the pack kernels index the bytes with them
     unsigned long long h_flags[4];
-    GBD_CUDA_TRY(cudaMemcpyAsync(h_flags, flags, sizeof h_flags, cudaMemcpyDeviceToHost, st));
+    GBD_CUDA_TRY(cudaMemcpyAsync(h_flags, flags, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     GBD_CUDA_TRY(cudaStreamSynchronize(st));
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < 2; ++s)
         if (h_flags[s] != ~0ull)
             return fail(GBD_EINVAL, std::string("gbd_tile_noalloc: read ") + std::to_string(h_flags[s]) +
                                         " of " + (s ? "B" : "A") +
                                         " is longer than max_len or its offsets decrease");
+    GBD_CUDA_TRY(launch_pack(d_seqA, d_offA, nA, stride, wA, lA, flags + 2, st));
+    GBD_CUDA_TRY(launch_pack(d_seqB, d_offB, nB, stride, wB, lB, flags + 3, st));
+    GBD_CUDA_TRY(cudaMemcpyAsync(h_flags + 2, flags + 2, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    GBD_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int s = 0; s < 2; ++s)
         if (h_flags[2 + s] != ~0ull)
             return fail(GBD_EINVAL, std::string("gbd_tile_noalloc: byte at position ") +
                                         std::to_string(h_flags[2 + s]) + " of " + (s ? "B" : "A") +
                                         " is not one of A, C, G, T");
-    }
     GeneralJob job{{wA, lA, nA, stride}, {wB, lB, nB, stride}, 0, nA, 0, nB, ld, OUT_RECT, d_out};
     const Scoring sc{ctx->params.match, ctx->params.mismatch, ctx->params.gap, ctx->params.conversion,
                      ctx->params.gap_open};

@@ -20,7 +20,11 @@ __global__ void pack_kernel(const uint8_t *__restrict__ seq, const uint64_t *__r
         const uint64_t r = t / stride;
         const uint32_t w = (uint32_t)(t - r * stride);
         const uint64_t s = off[r];
-        const uint64_t L = off[r + 1] - s;
+        // callers validate the offsets first; a read whose offsets decrease or whose
+        // length exceeds the stride is packed as empty, so the bytes are never indexed
+        // past it
+        const uint64_t e = off[r + 1];
+        const uint64_t L = (e < s || e - s > (uint64_t)stride * kBasesPerWord) ? 0 : e - s;
         if (w == 0) len[r] = (uint16_t)L;
         uint32_t word = 0;
         const uint64_t k0 = (uint64_t)w * kBasesPerWord;
