@@ -48,6 +48,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--check-pairs", type=int, default=2_000_000,
+                    help="uniformly sampled pairs of the timed triangle compared with the oracle")
     ap.add_argument("--mode", choices=["allpairs", "batch", "serve", "mds", "components", "affine", "annotate"],
                     default="allpairs")
     ap.add_argument("--serve-requests", type=int, default=40,
@@ -168,9 +170,10 @@ def _oracle_cores():
     return os.cpu_count() or 1
 
 
-def cpu_oracle_sample(rs, seconds: float, seed: int = 7, gpu_pairs=None):
+def cpu_oracle_sample(rs, seconds: float, seed: int = 7, gpu_pairs=None, min_check: int = 0):
     """Time the CPU oracle on a bounded uniform sample of the workload's pairs; with
-    gpu_pairs (a function (i, j) -> the GPU's distances) also compare the last sample."""
+    gpu_pairs (a function (i, j) -> the GPU's distances) also compare the last sample,
+    grown with further uniformly drawn pairs (untimed) to at least min_check pairs."""
     import oracle
     n = rs.n
     L = rs.lengths.astype(np.float64)
@@ -196,8 +199,12 @@ def cpu_oracle_sample(rs, seconds: float, seed: int = 7, gpu_pairs=None):
            "sample": f"{k} uniformly sampled pairs of the same {n}-read workload, "
                      f"{cells:.3e} cells in {dt:.1f} s on {cores} host threads"}
     if gpu_pairs is not None:
+        if k < min_check:
+            xi, xj = sample(min_check - k, seed + 1000)
+            want = np.concatenate([want, oracle.pairs(rs, xi, xj, nthreads=cores)])
+            i, j = np.concatenate([i, xi]), np.concatenate([j, xj])
         got = np.asarray(gpu_pairs(i, j), dtype=np.uint16)
-        out["check"] = {"pairs_checked": int(k), "mismatches": int(np.count_nonzero(got != want))}
+        out["check"] = {"pairs_checked": int(len(i)), "mismatches": int(np.count_nonzero(got != want))}
     return out
 
 
@@ -476,10 +483,21 @@ def run_gbd(args):
         line["e2e"] = run_e2e(gbd, ctx, rs, dev, stream)
     elif rank == 0:
         line["e2e"] = None
-    if not args.no_cpu_baseline and rank == 0 and world == 1:
-        # the oracle's sample doubles as an exactness check of this very triangle
-        line["cpu_baseline"] = cpu_oracle_sample(rs, args.cpu_seconds, gpu_pairs=gpu_pairs)
-        line["spot_check"] = line["cpu_baseline"].pop("check")
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            # the oracle's sample doubles as an exactness check of this very triangle
+            line["cpu_baseline"] = cpu_oracle_sample(rs, args.cpu_seconds, gpu_pairs=gpu_pairs,
+                                                     min_check=args.check_pairs)
+            line["spot_check"] = line["cpu_baseline"].pop("check")
+        else:
+            # no timed baseline: still compare a fixed uniform sample of this very triangle
+            rng = np.random.default_rng(17)
+            ci = rng.integers(0, n - 1, size=20000)
+            cj = ci + 1 + (rng.random(20000) * (n - 1 - ci)).astype(np.int64)
+            chk = cpu_baseline_pairs(rs, ci, cj, got=gpu_pairs(ci, cj),
+                                     what="uniformly sampled pairs (exactness check only, untimed)")
+            line["spot_check"] = chk.pop("check")
+        line["exact"] = line["spot_check"]["mismatches"] == 0
     if args.serve_requests > 0 and rank == 0:
         # served-batch latency: Poisson arrivals against this set, resident
         ref = ctx.load(rs)
@@ -489,6 +507,10 @@ def run_gbd(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(world)
+    if rank == 0 and not line["exact"]:
+        print(f"bench: {line['spot_check']['mismatches']} of {line['spot_check']['pairs_checked']} "
+              "checked distances differ from the oracle", file=sys.stderr)
+        return 1
     return 0
 
 

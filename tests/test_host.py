@@ -88,6 +88,9 @@ def test_cpu_baseline_leg_checks_what_it_is_given():
     for fn, want in ((exact, 0), (one_wrong, 1)):
         out = bench.cpu_oracle_sample(rs, 0.05, gpu_pairs=fn)
         assert out["kind"] == "oracle" and out["value"] > 0 and out["check"]["mismatches"] == want
+        # the check grows past the timed sample to the requested number of pairs
+        out = bench.cpu_oracle_sample(rs, 0.05, gpu_pairs=fn, min_check=6000)
+        assert out["check"]["pairs_checked"] >= 6000 and out["check"]["mismatches"] == want
 
     i = np.arange(0, 40)
     j = np.arange(1, 41)
