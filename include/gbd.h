@@ -142,13 +142,19 @@ int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns,
               uint16_t *const *d_tris, void *stream);
 
 /* (No paper counterpart: the tuning of this library's batched launch.)  The batched launch
- * tunes itself online: the first calls with a new list of samples and
- * outputs run the launch group with work units of 1, 0.5 and 2 times the cost model's size
- * (timed with events on `stream`; each of these calls first waits for the previous one to
- * finish), and from the fourth call on the fastest is replayed as a CUDA graph.  Results are
- * identical for every candidate.  gbd_batch_tuning reports the three timings (ms, 0 until
- * measured), the scale in use and whether tuning has finished; ENOTFOUND before any batch. */
-int gbd_batch_tuning(const gbd_ctx *ctx, double *trial_ms, double *scale, int *done);
+ * tunes itself online.  A candidate fixes the shape of the launch group: the work-unit size
+ * (subjects per unit, as a multiple of the cost model's size) and the number of streams the
+ * per-length-bucket launches alternate over.  The first five calls with a new list of
+ * samples and outputs run one candidate each, timed with events on `stream` (each of these
+ * calls first waits for the previous one to finish): scales 1, 0.5 and 2 with two streams,
+ * then the fastest scale with one and with three streams; from the sixth call on the
+ * fastest candidate is replayed as a CUDA graph.  Results are identical for every
+ * candidate.  gbd_batch_tuning reports, for up to `capacity` candidates, the timings (ms,
+ * 0 until measured), scales and stream counts (any array may be NULL), the number of
+ * candidates, the one chosen (-1 while tuning) and whether tuning has finished;
+ * ENOTFOUND before any batch. */
+int gbd_batch_tuning(const gbd_ctx *ctx, uint32_t capacity, double *trial_ms, double *trial_scale,
+                     int32_t *trial_streams, uint32_t *ntrials, int32_t *chosen, int *done);
 
 /* Query rows against a resident reference set (section 4.3: the distances between every
  * read of a sample and the ~2e3 annotated reads of a reference database, computed as a

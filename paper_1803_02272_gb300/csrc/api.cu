@@ -139,7 +139,7 @@ static int all_pairs_systolic(gbd_ctx *ctx, gbd_set *set, uint16_t *d_tri, cudaS
     job.gap_open = ctx->params.gap_open;
     SysJob *d_job = nullptr;
     if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
-    rc = run_systolic(d_job, sc.plan, ctx->sm_count, st, ctx->aux, ctx->fork, ctx->join, job.gap_open > 0);
+    rc = run_systolic(d_job, sc.plan, ctx->sm_count, st, &ctx->streams, kDefaultAuxStreams, job.gap_open > 0);
     cudaFreeAsync(d_job, st);
     if (rc != GBD_OK) return rc;
     return long_rows_general(ctx, set, d_tri, st);
@@ -191,7 +191,7 @@ static int tile_impl(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, c
         if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
         if ((rc = build_plan(entries, rows, plan, false, st, 0, B->mean_len, ctx->sm_count)) != GBD_OK)
             return rc;
-        rc = run_systolic(d_job, plan, ctx->sm_count, st, ctx->aux, ctx->fork, ctx->join, job.gap_open > 0);
+        rc = run_systolic(d_job, plan, ctx->sm_count, st, &ctx->streams, kDefaultAuxStreams, job.gap_open > 0);
         cudaFreeAsync(d_job, st);
         free_plan(plan, st);
         if (rc != GBD_OK) return rc;
@@ -248,7 +248,7 @@ static int band_impl(gbd_ctx *ctx, const gbd_set *set, uint64_t a0, uint64_t a1,
         if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
         if ((rc = build_plan(entries, rows, plan, false, st, 0, set->mean_len, ctx->sm_count)) != GBD_OK)
             return rc;
-        rc = run_systolic(d_job, plan, ctx->sm_count, st, ctx->aux, ctx->fork, ctx->join, job.gap_open > 0);
+        rc = run_systolic(d_job, plan, ctx->sm_count, st, &ctx->streams, kDefaultAuxStreams, job.gap_open > 0);
         cudaFreeAsync(d_job, st);
         free_plan(plan, st);
         if (rc != GBD_OK) return rc;
@@ -279,11 +279,18 @@ static int check_threshold(const gbd_threshold *th)
 
 
 // Last captured batch: its inputs, persistent job table and plan, and the graph.
-// Online autotuner of the batched launch: the first calls with a new set of samples
-// replay the launch group built with each candidate work-unit size (the cost model's
-// piece times kPieceScales[t]), timed with events; the next call keeps the fastest.
-constexpr int kTrials = 3;
-constexpr double kPieceScales[kTrials] = {1.0, 0.5, 2.0};
+// Online autotuner of the batched launch.  A candidate sets the shape of the launch group:
+// the work-unit size (the cost model's piece times `scale`) and the number of streams the
+// per-bucket launches alternate over (1 + naux).  Coordinate descent over the first calls
+// with a new list of samples, each timed with events: scales 1, 0.5 and 2 with two
+// streams, then the best scale with one and with three streams; the next call keeps the
+// fastest candidate.
+struct TuneCand {
+    double scale;
+    int naux;
+};
+constexpr int kTrials = 5;
+constexpr TuneCand kFirstCands[3] = {{1.0, 1}, {0.5, 1}, {2.0, 1}};
 
 struct BatchGraph {
     std::vector<uint64_t> ids;
@@ -294,15 +301,17 @@ struct BatchGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t kernels = 0;
-    // inputs of the plan, kept to rebuild it with another piece scale
+    // inputs of the plan, kept to rebuild it with another candidate
     std::vector<SysEntry> entries;
     std::vector<uint8_t> rows;
     double mean_len = 0.0;
     // autotuner state
+    TuneCand cands[kTrials] = {kFirstCands[0], kFirstCands[1], kFirstCands[2], {1.0, 0}, {1.0, 2}};
     int trial = 0;                    // candidate being timed; kTrials = tuning finished
     bool timing = false;              // events t0/t1 bracket the last launch
-    double trial_ms[kTrials] = {0, 0, 0};
-    double scale = 1.0;               // piece scale of the current graph
+    double trial_ms[kTrials] = {0, 0, 0, 0, 0};
+    int current = 0;                  // candidate of the recorded graph
+    int chosen = -1;                  // fastest candidate, once tuning has finished
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     int gap_open = 0;
     bool matches(const gbd_set *const *samples, uint64_t ns, uint16_t *const *d_tris, int conv, int go) const
@@ -331,7 +340,7 @@ void free_batch_cache(gbd_ctx *ctx)
 // Builds the batch's job table and plan (persistent) and records its launch group on the
 // context's capture stream.
 static int record_batch_graph(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const *samples, uint64_t ns,
-                              uint16_t *const *d_tris, double scale);
+                              uint16_t *const *d_tris, int cand);
 
 static int capture_batch(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const *samples, uint64_t ns,
                          uint16_t *const *d_tris)
@@ -383,25 +392,25 @@ static int capture_batch(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const *sam
     bg->rows.swap(rows);
     GBD_CUDA_TRY(cudaEventCreate(&bg->t0));
     GBD_CUDA_TRY(cudaEventCreate(&bg->t1));
-    return record_batch_graph(ctx, bg, samples, ns, d_tris, kPieceScales[0]);
+    return record_batch_graph(ctx, bg, samples, ns, d_tris, 0);
 }
 
-// (Re)builds the plan with the given piece scale and records the launch group as a graph.
-// The previous graph, if any, must have finished.
+// (Re)builds the plan with candidate `cand`'s piece scale and records the launch group,
+// over its number of streams, as a graph.  The previous graph, if any, must have finished.
 static int record_batch_graph(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const *samples, uint64_t ns,
-                              uint16_t *const *d_tris, double scale)
+                              uint16_t *const *d_tris, int cand)
 {
     cudaStream_t cap = ctx->capture;
     if (bg->exec) { cudaGraphExecDestroy(bg->exec); bg->exec = nullptr; }
     if (bg->graph) { cudaGraphDestroy(bg->graph); bg->graph = nullptr; }
     free_plan(bg->plan, nullptr);
-    bg->scale = scale;
-    int rc = build_plan(bg->entries, bg->rows, bg->plan, true, cap, 0, bg->mean_len, ctx->sm_count, scale);
+    bg->current = cand;
+    const TuneCand &c = bg->cands[cand];
+    int rc = build_plan(bg->entries, bg->rows, bg->plan, true, cap, 0, bg->mean_len, ctx->sm_count, c.scale);
     if (rc != GBD_OK) return rc;
     const uint64_t launches0 = gbd_kernel_launches();
     GBD_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    rc = run_systolic(bg->d_jobs, bg->plan, ctx->sm_count, cap, ctx->aux, ctx->fork, ctx->join,
-                      ctx->params.gap_open > 0);
+    rc = run_systolic(bg->d_jobs, bg->plan, ctx->sm_count, cap, &ctx->streams, c.naux, ctx->params.gap_open > 0);
     for (uint64_t s = 0; s < ns && rc == GBD_OK; ++s) rc = long_rows_general(ctx, samples[s], d_tris[s], cap);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cap, &g);
@@ -465,10 +474,12 @@ int gbd_create(gbd_ctx **out, int device, const gbd_params *p)
     ctx->device = device;
     ctx->params = prm;
     cudaError_t e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
+    for (int k = 0; k < StreamSet::kMaxAux && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&ctx->streams.aux[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->streams.join[k], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->streams.fork, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         delete ctx;
         return cuda_fail(e, "gbd_create");
@@ -495,14 +506,15 @@ void gbd_destroy(gbd_ctx *ctx)
     cudaSetDevice(ctx->device);
     free_batch_cache(ctx);
     free_mds_cache(ctx);
-    for (cudaStream_t st : {ctx->aux, ctx->capture}) {
+    for (cudaStream_t st : {ctx->streams.aux[0], ctx->streams.aux[1], ctx->capture}) {
         if (st) {
             cudaStreamSynchronize(st);
             cudaStreamDestroy(st);
         }
     }
-    if (ctx->fork) cudaEventDestroy(ctx->fork);
-    if (ctx->join) cudaEventDestroy(ctx->join);
+    if (ctx->streams.fork) cudaEventDestroy(ctx->streams.fork);
+    for (cudaEvent_t ev : ctx->streams.join)
+        if (ev) cudaEventDestroy(ev);
     delete ctx;
 }
 
@@ -691,7 +703,8 @@ int gbd_tile_hits(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, cons
     }
     rc = tile_impl(ctx, A, a0, a1, B, b0, b1, rect, rld, st);
     if (rc == GBD_OK)
-        rc = launch_rect_epilogue(rect, rld, A->view(), a0, a1, B->view(), b0, b1, Threshold{th->num, th->den, th->abs_max},
+        rc = launch_rect_epilogue(rect, rld, A->view(), a0, a1, B->view(), b0, b1, B->max_len,
+                                  Threshold{th->num, th->den, th->abs_max},
                                   d_hits, d_hits ? hit_capacity : 0,
                                   reinterpret_cast<unsigned long long *>(d_hit_count), d_ref_labels, d_row_labels,
                                   ctx->sm_count, st);
@@ -717,7 +730,8 @@ int gbd_threshold_components(gbd_ctx *ctx, const gbd_set *set, const gbd_thresho
         // the whole triangle, kept for the caller, then one stream over it
         if (m > 0) rc = all_pairs_impl(ctx, set, d_tri, st);
         if (rc == GBD_OK)
-            rc = launch_tri_components(d_tri, set->view(), t, d_labels, reinterpret_cast<unsigned long long *>(d_edges),
+            rc = launch_tri_components(d_tri, set->view(), set->max_len, t, d_labels,
+                                       reinterpret_cast<unsigned long long *>(d_edges),
                                        ctx->sm_count, st);
         return rc;
     }
@@ -738,7 +752,8 @@ int gbd_threshold_components(gbd_ctx *ctx, const gbd_set *set, const gbd_thresho
             break;
         }
         rc = band_impl(ctx, set, a0, a1, rect, ld, st);
-        if (rc == GBD_OK) rc = band_forest_add(bf, rect, ld, set->view(), a0, a1, t, d_labels, ctx->sm_count, st);
+        if (rc == GBD_OK)
+            rc = band_forest_add(bf, rect, ld, set->view(), a0, a1, set->max_len, t, d_labels, ctx->sm_count, st);
         a0 = a1;
     }
     const int erc = band_forest_end(bf, d_labels, n, reinterpret_cast<unsigned long long *>(d_edges), ctx->sm_count, st);
@@ -766,7 +781,8 @@ int gbd_rect_hits(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, cons
     if (d_hit_count) GBD_CUDA_TRY(cudaMemsetAsync(d_hit_count, 0, sizeof(uint64_t), st));
     if (d_row_labels && a1 > a0) GBD_CUDA_TRY(cudaMemsetAsync(d_row_labels, 0xff, (a1 - a0) * sizeof(int32_t), st));
     if (a0 == a1 || b0 == b1) return GBD_OK;
-    return launch_rect_epilogue(d_rect, ld, A->view(), a0, a1, B->view(), b0, b1, Threshold{th->num, th->den, th->abs_max},
+    return launch_rect_epilogue(d_rect, ld, A->view(), a0, a1, B->view(), b0, b1, B->max_len,
+                                Threshold{th->num, th->den, th->abs_max},
                                 d_hits, d_hits ? hit_capacity : 0, reinterpret_cast<unsigned long long *>(d_hit_count),
                                 d_ref_labels, d_row_labels, ctx->sm_count, st);
 }
@@ -784,7 +800,7 @@ int gbd_tri_components(gbd_ctx *ctx, const gbd_set *set, const uint16_t *d_tri, 
     cudaStream_t st = (cudaStream_t)stream;
     if (d_edges) GBD_CUDA_TRY(cudaMemsetAsync(d_edges, 0, sizeof(uint64_t), st));
     if (n == 0) return GBD_OK;
-    return launch_tri_components(d_tri, set->view(), Threshold{th->num, th->den, th->abs_max}, d_labels,
+    return launch_tri_components(d_tri, set->view(), set->max_len, Threshold{th->num, th->den, th->abs_max}, d_labels,
                                  reinterpret_cast<unsigned long long *>(d_edges), ctx->sm_count, st);
 }
 
@@ -839,17 +855,23 @@ int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns, uint16_t
             bg->trial_ms[bg->trial] = ms;
             bg->timing = false;
             ++bg->trial;
+            if (bg->trial == 3) {               // the stream-count trials take the best scale
+                int bs = 0;
+                for (int t = 1; t < 3; ++t)
+                    if (bg->trial_ms[t] < bg->trial_ms[bs]) bs = t;
+                bg->cands[3].scale = bg->cands[4].scale = bg->cands[bs].scale;
+            }
         }
-        double next = kPieceScales[0];
+        int next;
         if (bg->trial < kTrials) {
-            next = kPieceScales[bg->trial];
+            next = bg->trial;
         } else {
-            int best = 0;
+            next = 0;
             for (int t = 1; t < kTrials; ++t)
-                if (bg->trial_ms[t] < bg->trial_ms[best]) best = t;
-            next = kPieceScales[best];
+                if (bg->trial_ms[t] < bg->trial_ms[next]) next = t;
+            bg->chosen = next;
         }
-        if (next != bg->scale || bg->trial < kTrials) {
+        if (next != bg->current || bg->trial < kTrials) {
             rc = record_batch_graph(ctx, bg, samples, ns, d_tris, next);
             if (rc != GBD_OK) {
                 free_batch_cache(ctx);
@@ -869,14 +891,19 @@ int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns, uint16_t
     return GBD_OK;
 }
 
-int gbd_batch_tuning(const gbd_ctx *ctx, double *trial_ms, double *scale, int *done)
+int gbd_batch_tuning(const gbd_ctx *ctx, uint32_t capacity, double *trial_ms, double *trial_scale,
+                     int32_t *trial_streams, uint32_t *ntrials, int32_t *chosen, int *done)
 {
     if (!ctx) return fail(GBD_EINVAL, "gbd_batch_tuning: NULL context");
     const BatchGraph *bg = static_cast<const BatchGraph *>(ctx->batch_cache);
     if (!bg) return fail(GBD_ENOTFOUND, "gbd_batch_tuning: no batch has run on this context");
-    for (int t = 0; t < kTrials; ++t)
+    for (int t = 0; t < kTrials && (uint32_t)t < capacity; ++t) {
         if (trial_ms) trial_ms[t] = bg->trial_ms[t];
-    if (scale) *scale = bg->scale;
+        if (trial_scale) trial_scale[t] = bg->cands[t].scale;
+        if (trial_streams) trial_streams[t] = 1 + bg->cands[t].naux;
+    }
+    if (ntrials) *ntrials = kTrials;
+    if (chosen) *chosen = bg->chosen;
     if (done) *done = bg->trial >= kTrials ? 1 : 0;
     return GBD_OK;
 }

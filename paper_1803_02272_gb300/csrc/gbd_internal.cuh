@@ -76,6 +76,16 @@ struct SysPlan {
     }
 };
 
+// Streams over which consecutive bucket launches of the systolic kernel alternate: the
+// caller's stream, then aux[0], aux[1], ...; they fork from the caller's stream on `fork`
+// and join back into it on join[k].
+struct StreamSet {
+    static constexpr int kMaxAux = 2;
+    cudaStream_t aux[kMaxAux] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kMaxAux] = {};
+};
+
 // Device-resident schedule of a read set for the all-pairs triangle: one systolic entry
 // per read i short enough to be a systolic query (subjects i+1 .. n-1, in the set's own
 // order, so a warp writes a contiguous run of triangle row i), and the list of the
@@ -95,8 +105,7 @@ struct gbd_ctx {
     int device = 0;
     gbd_params params{};
     int sm_count = 0;
-    cudaStream_t aux = nullptr;       // second stream for overlapping bucket launches
-    cudaEvent_t fork = nullptr, join = nullptr;   // fork / join of aux with the caller's stream
+    gbd::StreamSet streams;           // extra streams for overlapping bucket launches
     cudaStream_t capture = nullptr;   // stream that records batch graphs
     void *batch_cache = nullptr;      // last captured batch graph (api.cu)
     // gbd_mds's fp16 square (ld^2 entries, 20 GB at n = 10^5), kept between calls: the
@@ -167,15 +176,17 @@ struct Threshold {
 // Rectangle D[r][c] = out[(r-a0)*ld + (c-b0)], r in [a0,a1), c in [b0,b1): hits appended
 // to hits (3 words each, up to cap; every hit counted in *count), and row annotation
 // from col_labels into row_labels (by r - a0) when both are set.
+// colmax_len: an upper bound of the column reads' lengths (the set's longest read).
 int launch_rect_epilogue(const uint16_t *out, uint64_t ld, const DeviceReads &A, uint64_t a0, uint64_t a1,
-                         const DeviceReads &B, uint64_t b0, uint64_t b1, const Threshold &th, uint32_t *hits,
-                         uint64_t cap, unsigned long long *count, const int32_t *col_labels,
+                         const DeviceReads &B, uint64_t b0, uint64_t b1, uint32_t colmax_len, const Threshold &th,
+                         uint32_t *hits, uint64_t cap, unsigned long long *count, const int32_t *col_labels,
                          int32_t *row_labels, int sm_count, cudaStream_t st);
 // Triangle of a set: every hit pair (i, j) is joined in the union-find forest `parent`
 // (which starts as parent[i] = i) and counted in *count (if set); then every read is
 // pointed at its root, the smallest read of its component.
-int launch_tri_components(const uint16_t *tri, const DeviceReads &S, const Threshold &th, uint32_t *parent,
-                          unsigned long long *count, int sm_count, cudaStream_t st);
+// max_len: the set's longest read.
+int launch_tri_components(const uint16_t *tri, const DeviceReads &S, uint32_t max_len, const Threshold &th,
+                          uint32_t *parent, unsigned long long *count, int sm_count, cudaStream_t st);
 
 // Threshold-graph components without the whole triangle: the caller computes the
 // distances of one band of rows [a0, a1) at a time into a rectangle whose row a0 + rr
@@ -193,7 +204,7 @@ struct BandForest {
 int band_forest_begin(BandForest &bf, const DeviceReads &S, const Threshold &th, uint32_t *parent, uint64_t max_entries,
                       int sm_count, cudaStream_t st);
 int band_forest_add(BandForest &bf, const uint16_t *rect, uint64_t ld, const DeviceReads &S, uint64_t a0, uint64_t a1,
-                    const Threshold &th, uint32_t *parent, int sm_count, cudaStream_t st);
+                    uint32_t max_len, const Threshold &th, uint32_t *parent, int sm_count, cudaStream_t st);
 int band_forest_end(BandForest &bf, uint32_t *parent, uint64_t n, unsigned long long *count, int sm_count,
                     cudaStream_t st);
 

@@ -36,10 +36,18 @@ namespace {
 
 enum ReqState { REQ_QUEUED = 0, REQ_ACTIVE = 1, REQ_DONE = 2, REQ_FAILED = 3 };
 
-// Pairs per chunk batch: about 0.15 s of GPU work when few pairs wait (latency), up to
-// 64 Mi pairs when much work is queued (fewer, larger batches keep the GPU saturated).
+// Pairs per chunk batch: about 0.15 s of GPU work when few pairs wait, an eighth of the
+// waiting work up to 64 Mi pairs otherwise (a newly arrived small request waits at most
+// for a slot to free, so the batch length bounds its latency), and up to 256 Mi pairs
+// when a backlog of kBacklog requests or more is waiting: a batch's launches then hold
+// more queries per length bucket, so their work units are longer (twice the cost
+// model's piece) and the per-unit pipeline fill and the launch tails cost a smaller
+// share than in one launch per request.
 constexpr uint64_t kChunkPairs = 12u << 20;
 constexpr uint64_t kMaxChunkPairs = 64u << 20;
+constexpr uint64_t kBacklogChunkPairs = 256u << 20;
+constexpr size_t kBacklog = 8;
+constexpr double kBacklogPieceScale = 2.0;
 constexpr double kAgeSeconds = 1.0;    // waiting time that halves a request's sort key
 constexpr int kSlots = 2;                     // chunk batches in flight
 
@@ -84,6 +92,7 @@ struct gbd_server {
     gbd_ctx *ctx = nullptr;
     const gbd_set *ref = nullptr;
     cudaStream_t slots[kSlots] = {};
+    gbd::StreamSet slot_aux[kSlots];           // a second stream per slot for bucket launches
     bool slot_busy[kSlots] = {};
     cudaStream_t ingest = nullptr;             // packing and batch uploads
     cudaEvent_t uploaded[kSlots] = {};         // a slot's uploads are complete
@@ -174,7 +183,7 @@ std::string admit(gbd_server *srv, Request *r)
 
 // Launches one batch of pieces on stream st; returns an error message or "".
 std::string launch_batch(gbd_server *srv, const std::vector<Piece> &pieces, cudaStream_t st,
-                         cudaEvent_t uploaded)
+                         const StreamSet *aux, cudaEvent_t uploaded)
 {
     gbd_ctx *ctx = srv->ctx;
     const gbd_set *ref = srv->ref;
@@ -237,7 +246,8 @@ std::string launch_batch(gbd_server *srv, const std::vector<Piece> &pieces, cuda
         if (cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(SysJob), cudaMemcpyHostToDevice, up) !=
             cudaSuccess)
             return "H2D failed";
-        if (build_plan(entries, rows, plan, false, up, 0, ref->mean_len, ctx->sm_count) != GBD_OK)
+        const double scale = (uint64_t)entries.size() * ref->n > kMaxChunkPairs ? kBacklogPieceScale : 1.0;
+        if (build_plan(entries, rows, plan, false, up, 0, ref->mean_len, ctx->sm_count, scale) != GBD_OK)
             return gbd_last_error();
     }
     if (cudaEventRecord(uploaded, up) != cudaSuccess || cudaStreamWaitEvent(st, uploaded, 0) != cudaSuccess)
@@ -247,7 +257,7 @@ std::string launch_batch(gbd_server *srv, const std::vector<Piece> &pieces, cuda
     for (const GeneralJob &gj : general)
         if (err.empty() && run_general(gj, sc, ctx->sm_count, st) != GBD_OK) err = gbd_last_error();
     if (err.empty() && !entries.empty() &&
-        run_systolic(d_jobs, plan, ctx->sm_count, st, nullptr, nullptr, nullptr, ctx->params.gap_open > 0) != GBD_OK)
+        run_systolic(d_jobs, plan, ctx->sm_count, st, aux, 1, ctx->params.gap_open > 0) != GBD_OK)
         err = gbd_last_error();
     plan.stream_ordered = true;
     free_plan(plan, st);
@@ -277,7 +287,8 @@ std::vector<Piece> next_pieces(gbd_server *srv)
     const uint64_t n_ref = srv->ref->n;
     uint64_t waiting = 0;
     for (Request *r : cand) waiting += (r->nq - r->next_query) * n_ref;
-    const uint64_t chunk = std::min(kMaxChunkPairs, std::max(kChunkPairs, waiting / 8));
+    const uint64_t cap = cand.size() >= kBacklog ? kBacklogChunkPairs : kMaxChunkPairs;
+    const uint64_t chunk = std::min(cap, std::max(kChunkPairs, waiting / 8));
     uint64_t room = std::max<uint64_t>(chunk / n_ref, 1);         // queries in this batch
     for (Request *r : cand) {
         if (room == 0) break;
@@ -335,7 +346,7 @@ void worker_main(gbd_server *srv)
             cudaStream_t st = srv->slots[s];
             std::string err;
             try {
-                err = launch_batch(srv, pieces, st, srv->uploaded[s]);
+                err = launch_batch(srv, pieces, st, &srv->slot_aux[s], srv->uploaded[s]);
             } catch (const std::exception &e) {
                 err = std::string("server batch: ") + e.what();
             }
@@ -382,7 +393,12 @@ int gbd_server_create(gbd_ctx *ctx, const gbd_set *ref, gbd_server **out)
     size_t free_b = 0, total_b = 0;
     GBD_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     srv->budget = ctx->params.hbm_budget ? ctx->params.hbm_budget : (uint64_t)(0.9 * (double)free_b);
-    for (int i = 0; i < kSlots; ++i) GBD_CUDA_TRY(cudaStreamCreateWithFlags(&srv->slots[i], cudaStreamNonBlocking));
+    for (int i = 0; i < kSlots; ++i) {
+        GBD_CUDA_TRY(cudaStreamCreateWithFlags(&srv->slots[i], cudaStreamNonBlocking));
+        GBD_CUDA_TRY(cudaStreamCreateWithFlags(&srv->slot_aux[i].aux[0], cudaStreamNonBlocking));
+        GBD_CUDA_TRY(cudaEventCreateWithFlags(&srv->slot_aux[i].fork, cudaEventDisableTiming));
+        GBD_CUDA_TRY(cudaEventCreateWithFlags(&srv->slot_aux[i].join[0], cudaEventDisableTiming));
+    }
     GBD_CUDA_TRY(cudaStreamCreateWithFlags(&srv->ingest, cudaStreamNonBlocking));
     for (int i = 0; i < kSlots; ++i) GBD_CUDA_TRY(cudaEventCreateWithFlags(&srv->uploaded[i], cudaEventDisableTiming));
     srv->worker = std::thread(worker_main, srv.get());
@@ -500,6 +516,13 @@ void gbd_server_destroy(gbd_server *srv)
             cudaStreamSynchronize(srv->slots[i]);
             cudaStreamDestroy(srv->slots[i]);
         }
+        StreamSet &a = srv->slot_aux[i];
+        if (a.aux[0]) {
+            cudaStreamSynchronize(a.aux[0]);
+            cudaStreamDestroy(a.aux[0]);
+        }
+        if (a.fork) cudaEventDestroy(a.fork);
+        if (a.join[0]) cudaEventDestroy(a.join[0]);
     }
     if (srv->ingest) {
         cudaStreamSynchronize(srv->ingest);

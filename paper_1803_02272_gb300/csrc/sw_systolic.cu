@@ -47,7 +47,7 @@ constexpr int CH = 16;                       // steps per chunk == lane skew
 // multiple of the 32 banks, so the lanes' 18-word stride stays conflict-free across the
 // ring's wrap.
 constexpr int RING_CHUNKS = 48;
-constexpr int RING = RING_CHUNKS * CH;       // 576 columns
+constexpr int RING = RING_CHUNKS * CH;       // 768 columns
 constexpr int SLOTS = RING + 3 * CH;         // ring index in [-16, RING + 32)
 // +2 pad words per 16 columns; arrays start on 32-word (128-byte) boundaries so every
 // lane's bank position depends on its column alone
@@ -99,80 +99,101 @@ struct SysUnit {
     uint32_t job, q, sub_begin, nsub;
 };
 
-// Warp-uniform cursor over one half's subject stream.  rem = bases of the current subject
-// from the current chunk on; wp = the subject's packed words.
-struct Cursor {
-    uint32_t pos, cnt, ck, rem, len, next_orig, next_len;
-    const uint32_t *wp;
+// Stream descriptors.  Half h of the stream (h = 0: the low 16 bits of every register,
+// h = 1: the high 16 bits) takes the unit's subjects at list positions h, h+2, h+4, ...;
+// each subject fills ceil(len/16) chunks of 16 columns (an empty subject one padding
+// chunk) and a finished half continues with padding chunks.  Every 16 chunks the warp
+// describes the next 16 chunks of both halves at once: lane t of half h (lanes 0-15:
+// h = 0, lanes 16-31: h = 1) works out chunk 16b + t of half h from the subject lengths
+// by a prefix sum over the half's lanes, writes the chunk's metadata into the table, and
+// keeps the chunk's packed word and valid-column count for the profile refill.
+struct HalfCursor {
+    uint32_t pos;      // list position (within the half) of the subject of chunk 16b
+    uint32_t ck;       // chunk of that subject
+    uint32_t cnt;      // subjects in the half
 };
 
-__device__ __forceinline__ void subject_at(const SysJob &J, uint32_t list_index, uint32_t &orig,
-                                           uint32_t &len)
+// Describes chunks [b16, b16 + 16) of this lane's half.  tslot = b16 mod RING_CHUNKS (the
+// table slot of chunk b16; b16 is a multiple of 16, so tslot + t never wraps).  Sets C to
+// the first chunk where both halves are padding, once such a chunk appears.
+__device__ __forceinline__ void describe_chunks(const SysJob &J, const SysUnit &u, int lane, HalfCursor &hc,
+                                                uint32_t b16, int tslot, uint32_t *table, uint32_t &word,
+                                                uint32_t &nvpair, int &C)
 {
-    orig = J.sub_perm ? __ldg(J.sub_perm + list_index) : list_index;
-    len = __ldg(J.S.len + orig);
-}
-
-__device__ __forceinline__ void cursor_init(Cursor &cu, const SysJob &J, const SysUnit &u, int h)
-{
-    cu.cnt = (u.nsub + 1 - h) >> 1;            // half h takes list positions h, h+2, ...
-    cu.pos = 0;
-    cu.ck = 0;
-    uint32_t orig = 0;
-    cu.len = 0;
-    if (cu.cnt > 0) subject_at(J, u.sub_begin + h, orig, cu.len);
-    cu.rem = cu.len;
-    cu.wp = J.S.words + (uint64_t)orig * J.S.stride;
-    if (cu.cnt > 1) subject_at(J, u.sub_begin + h + 2, cu.next_orig, cu.next_len);
-    else { cu.next_orig = 0; cu.next_len = 0; }
-}
-
-__device__ __forceinline__ void cursor_advance(Cursor &cu, const SysJob &J, const SysUnit &u, int h)
-{
-    if (cu.pos >= cu.cnt) return;
-    ++cu.ck;
-    if (cu.rem > 16u) {                        // another chunk of the same subject
-        cu.rem -= 16u;
-        return;
+    const uint32_t t = lane & 15, h = lane >> 4;
+    // the subject t positions after the current one
+    const uint32_t pt = hc.pos + t;
+    uint32_t orig = 0, len = 0, nch = 1u << 16;          // past the end: one endless padding run
+    if (pt < hc.cnt) {
+        const uint32_t li = u.sub_begin + h + 2 * pt;
+        orig = J.sub_perm ? __ldg(J.sub_perm + li) : li;
+        len = __ldg(J.S.len + orig);
+        nch = max(1u, (len + 15u) >> 4);
     }
-    cu.ck = 0;
-    ++cu.pos;
-    cu.len = cu.next_len;
-    cu.rem = cu.next_len;
-    cu.wp = J.S.words + (uint64_t)cu.next_orig * J.S.stride;
-    if (cu.pos + 1 < cu.cnt) subject_at(J, u.sub_begin + h + 2 * (cu.pos + 1), cu.next_orig, cu.next_len);
+    // E = chunk (relative to b16) that follows subject pt: inclusive prefix sum of the
+    // chunk counts, the current subject's consumed chunks taken off
+    uint32_t E = nch - (t == 0 ? hc.ck : 0u);
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, E, d, 16);
+        if (t >= (uint32_t)d) E += o;
+    }
+    // E >= t + 1 for every lane, so the subject of chunk b16 + t is the number of subject
+    // ends at relative chunks <= t (never more than t), and it starts at the last of them
+    const uint32_t mark = E < 16u ? (1u << (E + 16u * h)) : 0u;
+    const uint32_t ends = (__reduce_or_sync(0xffffffffu, mark) >> (16u * h)) & ((2u << t) - 1u);
+    const uint32_t si = __popc(ends);
+    const uint32_t start = ends ? 31u - __clz(ends) : 0u;
+    const uint32_t ckt = t - start + (si == 0 ? hc.ck : 0u);
+    const uint32_t slen = __shfl_sync(0xffffffffu, len, (int)si, 16);
+    const uint32_t sorig = __shfl_sync(0xffffffffu, orig, (int)si, 16);
+    const uint32_t p = hc.pos + si;
+    const bool valid = p < hc.cnt;
+    const uint32_t rem = slen - 16u * ckt;
+    const bool first = valid && ckt == 0;
+    const bool last = valid && rem <= 16u;
+    const uint32_t nv = valid ? min(16u, rem) : 0u;
+    word = valid ? __ldg(J.S.words + (uint64_t)sorig * J.S.stride + ckt) : 0u;
+    // the table entry of chunk b16 + t joins both halves: exchange with lane t ^ 16
+    const uint32_t fa = (first ? 1u : 0u) | (last ? 2u : 0u) | (nv << 2);
+    const uint32_t fb = (valid ? slen : 0u) | (p << 16);
+    const uint32_t ga = __shfl_xor_sync(0xffffffffu, fa, 16);
+    const uint32_t gb = __shfl_xor_sync(0xffffffffu, fb, 16);
+    const uint32_t alo = h ? ga : fa, ahi = h ? fa : ga;
+    const uint32_t blo = h ? gb : fb, bhi = h ? fb : gb;
+    nvpair = (alo >> 2) | ((ahi >> 2) << 8);
+    if (h == 0) {
+        uint4 e;
+        e.x = ((alo & 1u) ? 0x0000ffffu : 0u) | ((ahi & 1u) ? 0xffff0000u : 0u);
+        e.y = ((alo & 2u) ? 0x0000ffffu : 0u) | ((ahi & 2u) ? 0xffff0000u : 0u);
+        e.z = (blo & 0xffffu) | (bhi << 16);
+        e.w = (blo >> 16) | (bhi & 0xffff0000u);
+        *reinterpret_cast<uint4 *>(table + 4 * (tslot + (int)t)) = e;
+    }
+    // state at chunk b16 + 16, from the half's lane 15
+    const uint32_t nxt = last ? (p + 1u) : (p | (valid ? (ckt + 1u) << 16 : 0u));
+    const uint32_t n15 = __shfl_sync(0xffffffffu, nxt, 15, 16);
+    hc.pos = n15 & 0xffffu;
+    hc.ck = n15 >> 16;
+    // first chunk where both halves are padding
+    const uint32_t vb = __ballot_sync(0xffffffffu, valid);
+    const uint32_t both = ~(vb | (vb >> 16)) & 0xffffu;
+    if (C < 0 && both != 0u) C = (int)b16 + __ffs(both) - 1;
 }
 
-// Stream metadata + packed word of the chunk a cursor points at.
-struct ChunkInfo {
-    uint32_t word;      // 16 bases, 2 bits each
-    uint32_t nvalid;    // valid columns in this chunk (0 = padding chunk)
-    uint32_t first, last;
-    uint32_t len, pos;
-};
-
-__device__ __forceinline__ void cursor_chunk(const Cursor &cu, const SysJob &J, ChunkInfo &ci)
-{
-    const bool valid = cu.pos < cu.cnt;
-    ci.first = valid && cu.ck == 0;
-    ci.last = valid && cu.rem <= 16u;          // an empty subject is one padding chunk
-    ci.pos = cu.pos;
-    ci.len = cu.len;
-    ci.nvalid = valid ? min(16u, cu.rem) : 0u;
-    ci.word = valid ? __ldg(cu.wp + cu.ck) : 0u;
-}
-
-// Write chunk X of the two half streams into the warp's profile ring and table.
-// m = X mod RING_CHUNKS, the ring slot of stream chunk X.  Both halves at once: the two
-// base codes of this lane's column sit in the halves of one word, a half equal to the
-// query base q gives s + 2 = 3, any other 1, a padding column the never-matching value.
-__device__ __forceinline__ void fill_chunk(uint32_t *ws, int lane, int m, const ChunkInfo &lo,
-                                           const ChunkInfo &hi)
+// Write chunk X of the two half streams into the warp's profile ring (slot m = X mod
+// RING_CHUNKS).  Both halves at once: the two base codes of this lane's column sit in the
+// halves of one word, a half equal to the query base q gives s + 2 = 3, any other 1, a
+// padding column the never-matching value.  nvpair = valid columns of the low half |
+// those of the high half << 8.
+__device__ __forceinline__ void fill_chunk(uint32_t *ws, int lane, int m, uint32_t wlo, uint32_t whi,
+                                           uint32_t nvpair)
 {
     const int x = lane & 15;
     const int qa = (lane >> 4) * 2;
-    const uint32_t codes = ((lo.word >> (2 * x)) & 3u) | (((hi.word >> (2 * x)) & 3u) << 16);
-    const uint32_t pad = ((uint32_t)x < lo.nvalid ? 0u : 0x0000ffffu) | ((uint32_t)x < hi.nvalid ? 0u : 0xffff0000u);
+    const uint32_t codes = ((wlo >> (2 * x)) & 3u) | (((whi >> (2 * x)) & 3u) << 16);
+    const uint32_t pad = ((uint32_t)x < (nvpair & 0xffu) ? 0u : 0x0000ffffu) |
+                         ((uint32_t)x < (nvpair >> 8) ? 0u : 0xffff0000u);
     const int rho = 16 * m + x;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
@@ -183,13 +204,6 @@ __device__ __forceinline__ void fill_chunk(uint32_t *ws, int lane, int m, const 
         arr[pslot(rho)] = v;
         if (rho < 32) arr[pslot(rho + RING)] = v;
         if (rho >= RING - 16) arr[pslot(rho - RING)] = v;
-    }
-    if (lane == 0) {
-        uint32_t *e = ws + TABLE_OFF + 4 * m;
-        e[0] = (lo.first ? 0x0000ffffu : 0u) | (hi.first ? 0xffff0000u : 0u);
-        e[1] = (lo.last ? 0x0000ffffu : 0u) | (hi.last ? 0xffff0000u : 0u);
-        e[2] = lo.len | (hi.len << 16);
-        e[3] = (lo.pos & 0xffffu) | (hi.pos << 16);       // position in each half's list
     }
 }
 
@@ -206,20 +220,18 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
     const int la = J.Q.len[u.q];
     const uint32_t *qwords = J.Q.words + (uint64_t)u.q * J.Q.stride;
 
-    // ---- stream cursors (warp-uniform) and the first two chunks of the ring
-    Cursor cur_lo, cur_hi;
-    cursor_init(cur_lo, J, u, 0);
-    cursor_init(cur_hi, J, u, 1);
-    ChunkInfo ci_lo, ci_hi;
-    cursor_chunk(cur_lo, J, ci_lo);
-    cursor_chunk(cur_hi, J, ci_hi);
-    fill_chunk(ws, lane, 0, ci_lo, ci_hi);        // ring slot 0
-    cursor_advance(cur_lo, J, u, 0);
-    cursor_advance(cur_hi, J, u, 1);
-    cursor_chunk(cur_lo, J, ci_lo);           // pending: chunk 1
-    cursor_chunk(cur_hi, J, ci_hi);
+    // ---- stream descriptors of chunks 0..15 and the first chunk of the ring
     int C = -1;                                // stream length in chunks, once known
-    if (cur_lo.pos >= cur_lo.cnt && cur_hi.pos >= cur_hi.cnt) C = 1;
+    HalfCursor hc;
+    hc.pos = 0;
+    hc.ck = 0;
+    hc.cnt = (u.nsub + 1 - (uint32_t)(lane >> 4)) >> 1;   // half h: list positions h, h+2, ...
+    uint32_t *const table = ws + TABLE_OFF;
+    uint32_t dword, dnv;                       // this lane's chunk of the current 16
+    int tslot = 0;                             // table slot of the first of those chunks
+    describe_chunks(J, u, lane, hc, 0u, 0, table, dword, dnv, C);
+    fill_chunk(ws, lane, 0, __shfl_sync(0xffffffffu, dword, 0), __shfl_sync(0xffffffffu, dword, 16),
+               __shfl_sync(0xffffffffu, dnv, 0));
     __syncwarp();
 
     // ---- per-row profile addresses
@@ -279,19 +291,14 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
     int m_fill = 1;
     int m_c = (RING_CHUNKS - lane % RING_CHUNKS) % RING_CHUNKS;
 
-    for (int g = 0; C < 0 || g < C + LANES; ++g) {
-        // ---- refill: pending chunk g+1 into the ring, then read ahead chunk g+2
-        fill_chunk(ws, lane, m_fill, ci_lo, ci_hi);
-        m_fill = (m_fill == RING_CHUNKS - 1) ? 0 : m_fill + 1;
-        cursor_advance(cur_lo, J, u, 0);
-        cursor_advance(cur_hi, J, u, 1);
-        cursor_chunk(cur_lo, J, ci_lo);
-        cursor_chunk(cur_hi, J, ci_hi);
-        if (C < 0 && cur_lo.pos >= cur_lo.cnt && cur_hi.pos >= cur_hi.cnt) C = g + 2;
-        __syncwarp();
-
+    // Two chunks per iteration: the second one's profile columns lie 18 words (72 bytes)
+    // after the first one's, so it reads them at immediate offsets, and the loop test,
+    // the rebase check and the per-row address advance run once per 32 steps.  Reading
+    // one chunk past the ring's last slot lands in the copy of slot 0 that every fill of
+    // slot 0 also writes.  An extra padding chunk at the end (C + LANES odd) emits nothing.
+    for (int g0 = 0; C < 0 || g0 < C + LANES; g0 += 2) {
         // ---- rebase every REBASE_CHUNKS chunks (all lanes at the same global step)
-        if (g > 0 && (g & (REBASE_CHUNKS - 1)) == 0) {
+        if (g0 > 0 && (g0 & (REBASE_CHUNKS - 1)) == 0) {
 #pragma unroll
             for (int r = 0; r < R; ++r) { V0[r] -= REBASE2; V1[r] -= REBASE2; }
 #pragma unroll
@@ -306,138 +313,157 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
             }
         }
 
-        // ---- this lane's chunk c: stream metadata
-        const int c = g - lane;
-        uint32_t Mfirst = 0, Mend;                 // Mend: chunk c-1 ended a subject
-        uint32_t lens_c = 0, pos_c = 0, Mlast_c = 0;
-        if (c >= 0) {
-            const uint32_t *e = ws + TABLE_OFF + 4 * m_c;
-            const uint4 ev = *reinterpret_cast<const uint4 *>(e);
-            Mfirst = ev.x; Mlast_c = ev.y; lens_c = ev.z;
-            pos_c = ev.w;
-        }
-        Mend = (c >= 1) ? Mlast_prev : 0xffffffffu;   // c <= 0: discard what came before
-        const uint32_t fbase = f_prev + ONE2;         // floor at step 0 of this chunk
-
-        // ---- 16 steps
+        const int m_c1 = (m_c == RING_CHUNKS - 1) ? 0 : m_c + 1;   // table slot of the second chunk
 #pragma unroll
-        for (int q = 0; q < CH; ++q) {
-            uint32_t *cur = (q & 1) ? V0 : V1;        // V(u-1)
-            uint32_t *nxt = (q & 1) ? V1 : V0;        // V(u-2) in, V(u) out
-            const uint32_t f = f_prev + ONE2;
-            // row R-1 of lane k-1, produced 1 + D steps ago
-            uint32_t up0 = __shfl_up_sync(0xffffffffu,
-                                          HIST ? hist[(q + CH - 1 - D) & (CH - 1)] : cur[R - 1], 1);
-            if (lane == 0) up0 = f_prev;              // top boundary: H(0, j) = 0
-            uint32_t fup0 = 0u;
-            if (AFFINE) {
-                fup0 = __shfl_up_sync(0xffffffffu, HISTF ? histF[(q + CH - 1 - D) & (CH - 1)] : Fh[R - 1], 1);
-                if (lane == 0) fup0 = NEG2;           // F(0, j) = minus infinity
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int g = g0 + h2;
+            // ---- refill: chunk g+1 into the ring (describing the next 16 chunks first when
+            // g+1 starts them; g+1 is odd for the first chunk of the pair)
+            if (h2 == 1 && ((g + 1) & 15) == 0) {
+                tslot = (tslot == RING_CHUNKS - 16) ? 0 : tslot + 16;
+                describe_chunks(J, u, lane, hc, (uint32_t)(g + 1), tslot, table, dword, dnv, C);
             }
-            uint32_t diag0 = up0_prev;
-#pragma unroll
-            for (int r = R - 1; r >= 0; --r) {
-                // this row's value one step ago (left input) and its new value
-                uint32_t &left = (HIST && r == R - 1) ? hist[(q + CH - 1) & (CH - 1)] : cur[r];
-                uint32_t &out = (HIST && r == R - 1) ? hist[q] : nxt[r];
-                if (r == q) {
-                    // row q reaches a subject's first column: its left input (and, for
-                    // row 0, its diagonal) become the floor of column 0.  Rows below
-                    // already read the old value as their "up" input this step.
-                    left = lop_sel(left, f_prev, Mfirst);
-                    if (AFFINE) Eh[r] = lop_sel(Eh[r], NEG2, Mfirst);      // E(i, 0) = -inf
-                    if (r == 0) diag0 = lop_sel(diag0, f_prev2, Mfirst);
-                }
-                const uint32_t up = r ? cur[r - 1] : up0;
-                const uint32_t dg = r ? nxt[r - 1] : diag0;
-                const uint32_t s2 = (((q - r) & 1) == 0) ? sp[r].x : sp[r].y;
-                const uint32_t E = vaddmax(dg, s2, f);
-                if (AFFINE) {
-                    const uint32_t fu = r ? Fh[r - 1] : fup0;
-                    const uint32_t eh = vaddmax(left, ngo, Eh[r]);
-                    const uint32_t fh = vaddmax(up, ngo, fu);
-                    out = vmax3(E, eh, fh);
-                    Eh[r] = eh;
-                    if (HISTF && r == R - 1) histF[q] = fh; else Fh[r] = fh;
-                } else {
-                    out = vmax3(up, left, E);
-                }
-                if (((q - r) & 1) != 0) sp[r] = lds64(ws, addr[r] + 4 * poff(q + 1 - r));
-            }
-            up0_prev = up0;
-            // best: rows <= q are in column chunk c, rows > q in chunk c-1
             {
-                const int nN = (q < R - 1 ? q : R - 1) + 1;
-                auto val = [&](int r) -> uint32_t { return (HIST && r == R - 1) ? hist[q] : nxt[r]; };
-                uint32_t mN = val(0);
+                const int src = (g + 1) & 15;
+                fill_chunk(ws, lane, m_fill, __shfl_sync(0xffffffffu, dword, src),
+                           __shfl_sync(0xffffffffu, dword, src + 16), __shfl_sync(0xffffffffu, dnv, src));
+            }
+            m_fill = (m_fill == RING_CHUNKS - 1) ? 0 : m_fill + 1;
+            __syncwarp();
+
+            // ---- this lane's chunk c: stream metadata
+            const int c = g - lane;
+            uint32_t Mfirst = 0, Mend;                 // Mend: chunk c-1 ended a subject
+            uint32_t lens_c = 0, pos_c = 0, Mlast_c = 0;
+            if (c >= 0) {
+                const uint32_t *e = table + 4 * (h2 ? m_c1 : m_c);
+                const uint4 ev = *reinterpret_cast<const uint4 *>(e);
+                Mfirst = ev.x; Mlast_c = ev.y; lens_c = ev.z;
+                pos_c = ev.w;
+            }
+            Mend = (c >= 1) ? Mlast_prev : 0xffffffffu;   // c <= 0: discard what came before
+            const uint32_t fbase = f_prev + ONE2;         // floor at step 0 of this chunk
+
+            // ---- 16 steps
 #pragma unroll
-                for (int r = 1; r < R; r += 2) {
-                    if (r < nN) {
-                        if (r + 1 < nN) mN = vmax3(mN, val(r), val(r + 1));
-                        else mN = vmax2(mN, val(r));
-                    }
+            for (int q = 0; q < CH; ++q) {
+                uint32_t *cur = (q & 1) ? V0 : V1;        // V(u-1)
+                uint32_t *nxt = (q & 1) ? V1 : V0;        // V(u-2) in, V(u) out
+                const uint32_t f = f_prev + ONE2;
+                // row R-1 of lane k-1, produced 1 + D steps ago
+                uint32_t up0 = __shfl_up_sync(0xffffffffu,
+                                              HIST ? hist[(q + CH - 1 - D) & (CH - 1)] : cur[R - 1], 1);
+                if (lane == 0) up0 = f_prev;              // top boundary: H(0, j) = 0
+                uint32_t fup0 = 0u;
+                if (AFFINE) {
+                    fup0 = __shfl_up_sync(0xffffffffu, HISTF ? histF[(q + CH - 1 - D) & (CH - 1)] : Fh[R - 1], 1);
+                    if (lane == 0) fup0 = NEG2;           // F(0, j) = minus infinity
                 }
-                curRel = vaddmax(mN, pack2(-q), curRel);
-                if (nN < R) {
-                    uint32_t mO = val(nN);
+                uint32_t diag0 = up0_prev;
+#pragma unroll
+                for (int r = R - 1; r >= 0; --r) {
+                    // this row's value one step ago (left input) and its new value
+                    uint32_t &left = (HIST && r == R - 1) ? hist[(q + CH - 1) & (CH - 1)] : cur[r];
+                    uint32_t &out = (HIST && r == R - 1) ? hist[q] : nxt[r];
+                    if (r == q) {
+                        // row q reaches a subject's first column: its left input (and, for
+                        // row 0, its diagonal) become the floor of column 0.  Rows below
+                        // already read the old value as their "up" input this step.
+                        left = lop_sel(left, f_prev, Mfirst);
+                        if (AFFINE) Eh[r] = lop_sel(Eh[r], NEG2, Mfirst);      // E(i, 0) = -inf
+                        if (r == 0) diag0 = lop_sel(diag0, f_prev2, Mfirst);
+                    }
+                    const uint32_t up = r ? cur[r - 1] : up0;
+                    const uint32_t dg = r ? nxt[r - 1] : diag0;
+                    const uint32_t s2 = (((q - r) & 1) == 0) ? sp[r].x : sp[r].y;
+                    const uint32_t E = vaddmax(dg, s2, f);
+                    if (AFFINE) {
+                        const uint32_t fu = r ? Fh[r - 1] : fup0;
+                        const uint32_t eh = vaddmax(left, ngo, Eh[r]);
+                        const uint32_t fh = vaddmax(up, ngo, fu);
+                        out = vmax3(E, eh, fh);
+                        Eh[r] = eh;
+                        if (HISTF && r == R - 1) histF[q] = fh; else Fh[r] = fh;
+                    } else {
+                        out = vmax3(up, left, E);
+                    }
+                    if (((q - r) & 1) != 0) sp[r] = lds64(ws, addr[r] + 72u * h2 + 4 * poff(q + 1 - r));
+                }
+                up0_prev = up0;
+                // best: rows <= q are in column chunk c, rows > q in chunk c-1
+                {
+                    const int nN = (q < R - 1 ? q : R - 1) + 1;
+                    auto val = [&](int r) -> uint32_t { return (HIST && r == R - 1) ? hist[q] : nxt[r]; };
+                    uint32_t mN = val(0);
 #pragma unroll
                     for (int r = 1; r < R; r += 2) {
-                        const int a = nN + r, b = nN + r + 1;
-                        if (a < R) {
-                            if (b < R) mO = vmax3(mO, val(a), val(b));
-                            else mO = vmax2(mO, val(a));
+                        if (r < nN) {
+                            if (r + 1 < nN) mN = vmax3(mN, val(r), val(r + 1));
+                            else mN = vmax2(mN, val(r));
                         }
                     }
-                    prevRel = vaddmax(mO, pack2(-q), prevRel);
-                }
-            }
-            f_prev2 = f_prev;
-            f_prev = f;
-        }
-
-        // ---- chunk end: fold chunk c-1, pass totals down the lanes, write results
-        {
-            uint32_t recv = __shfl_up_sync(0xffffffffu, emit, 1);
-            if (lane == 0) recv = 0;
-            const uint32_t negfb = __vsub2(0u, fbase);                 // -fbase in both halves
-            const uint32_t a = vaddmax(prevRel, negfb, acc);       // max(acc, prev - fbase)
-            const uint32_t total = vmax2(a, recv);
-            emit = lop_sel(emit, total, Mend);
-            acc = a & ~Mend;
-            prevRel = curRel + 16u * ONE2;
-            curRel = 0;
-            if (lane == LANES - 1 && c >= 1 && Mend != 0) {
-                const int conv = J.conversion;
+                    curRel = vaddmax(mN, pack2(-q), curRel);
+                    if (nN < R) {
+                        uint32_t mO = val(nN);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if ((Mend >> (16 * h)) & 1u) {
-                        const int S = (int)(int16_t)(total >> (16 * h));
-                        const uint32_t li = u.sub_begin + h + 2 * ((pos_prev >> (16 * h)) & 0xffffu);
-                        const uint32_t so = J.sub_perm ? __ldg(J.sub_perm + li) : li;
-                        const int lb = (int)((lens_prev >> (16 * h)) & 0xffffu);
-                        uint64_t idx;
-                        if (J.mode == OUT_TRI) {
-                            const uint64_t i = min((uint64_t)u.q, (uint64_t)so);
-                            const uint64_t j = max((uint64_t)u.q, (uint64_t)so);
-                            idx = i * J.n - i * (i + 1) / 2 + (j - i - 1);
-                        } else {
-                            idx = ((uint64_t)u.q - J.row0) * J.ld + ((uint64_t)so - J.col0);
+                        for (int r = 1; r < R; r += 2) {
+                            const int a = nN + r, b = nN + r + 1;
+                            if (a < R) {
+                                if (b < R) mO = vmax3(mO, val(a), val(b));
+                                else mO = vmax2(mO, val(a));
+                            }
                         }
-                        J.out[idx] = score_to_distance(S, la, lb, conv);
+                        prevRel = vaddmax(mO, pack2(-q), prevRel);
                     }
                 }
+                f_prev2 = f_prev;
+                f_prev = f;
             }
-            Mlast_prev = (c >= 0) ? Mlast_c : 0u;
-            lens_prev = lens_c;
-            pos_prev = pos_c;
+
+            // ---- chunk end: fold chunk c-1, pass totals down the lanes, write results
+            {
+                uint32_t recv = __shfl_up_sync(0xffffffffu, emit, 1);
+                if (lane == 0) recv = 0;
+                const uint32_t negfb = __vsub2(0u, fbase);                 // -fbase in both halves
+                const uint32_t a = vaddmax(prevRel, negfb, acc);       // max(acc, prev - fbase)
+                const uint32_t total = vmax2(a, recv);
+                emit = lop_sel(emit, total, Mend);
+                acc = a & ~Mend;
+                prevRel = curRel + 16u * ONE2;
+                curRel = 0;
+                if (lane == LANES - 1 && c >= 1 && Mend != 0) {
+                    const int conv = J.conversion;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if ((Mend >> (16 * h)) & 1u) {
+                            const int S = (int)(int16_t)(total >> (16 * h));
+                            const uint32_t li = u.sub_begin + h + 2 * ((pos_prev >> (16 * h)) & 0xffffu);
+                            const uint32_t so = J.sub_perm ? __ldg(J.sub_perm + li) : li;
+                            const int lb = (int)((lens_prev >> (16 * h)) & 0xffffu);
+                            uint64_t idx;
+                            if (J.mode == OUT_TRI) {
+                                const uint64_t i = min((uint64_t)u.q, (uint64_t)so);
+                                const uint64_t j = max((uint64_t)u.q, (uint64_t)so);
+                                idx = i * J.n - i * (i + 1) / 2 + (j - i - 1);
+                            } else {
+                                idx = ((uint64_t)u.q - J.row0) * J.ld + ((uint64_t)so - J.col0);
+                            }
+                            J.out[idx] = score_to_distance(S, la, lb, conv);
+                        }
+                    }
+                }
+                Mlast_prev = (c >= 0) ? Mlast_c : 0u;
+                lens_prev = lens_c;
+                pos_prev = pos_c;
+            }
         }
-        // ---- advance the profile addresses by one chunk
+        // ---- advance the profile addresses by two chunks
         {
-            const bool wrap = (m_c == RING_CHUNKS - 1);
-            const uint32_t d = wrap ? (uint32_t)(4 * 18 * (1 - RING_CHUNKS)) : (uint32_t)(4 * 18);
+            const bool wrap = (m_c >= RING_CHUNKS - 2);
+            const uint32_t d = wrap ? (uint32_t)(4 * 18 * (2 - RING_CHUNKS)) : (uint32_t)(4 * 18 * 2);
 #pragma unroll
             for (int r = 0; r < R; ++r) addr[r] += d;
-            m_c = wrap ? 0 : m_c + 1;
+            m_c = wrap ? m_c + 2 - RING_CHUNKS : m_c + 2;
         }
         (void)err;
     }
@@ -621,7 +647,7 @@ void free_plan(SysPlan &plan, cudaStream_t stream)
 }
 
 int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaStream_t stream,
-                 cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join, bool affine)
+                 const StreamSet *ss, int naux, bool affine)
 {
     if (plan.buckets.empty()) return GBD_OK;
     int prc = systolic_prepare();
@@ -630,13 +656,14 @@ int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaSt
     uint32_t *scratch = nullptr;                  // per bucket: work counter, error flags
     GBD_CUDA_TRY(cudaMallocAsync((void **)&scratch, 2 * nb * sizeof(uint32_t), stream));
     GBD_CUDA_TRY(cudaMemsetAsync(scratch, 0, 2 * nb * sizeof(uint32_t), stream));
-    // Buckets alternate between `stream` and `aux`, so the tail of one bucket's launch
-    // overlaps the start of the next (a persistent grid starts where the other's blocks
-    // have exited).  The two streams fork and join on events.
-    const bool two = aux != nullptr && fork != nullptr && join != nullptr && nb > 1;
-    if (two) {
-        GBD_CUDA_TRY(cudaEventRecord(fork, stream));
-        GBD_CUDA_TRY(cudaStreamWaitEvent(aux, fork, 0));
+    // Buckets alternate between `stream` and the aux streams, so the tail of one bucket's
+    // launch overlaps the start of the next (a persistent grid starts where the other's
+    // blocks have exited).  The streams fork and join on events.
+    int extra = (ss == nullptr || nb < 2) ? 0 : std::min(naux, StreamSet::kMaxAux);
+    extra = std::min<int>(extra, (int)nb - 1);
+    if (extra > 0) {
+        GBD_CUDA_TRY(cudaEventRecord(ss->fork, stream));
+        for (int k = 0; k < extra; ++k) GBD_CUDA_TRY(cudaStreamWaitEvent(ss->aux[k], ss->fork, 0));
     }
     int rc = GBD_OK;
     for (size_t i = 0; i < nb && rc == GBD_OK; ++i) {
@@ -645,7 +672,8 @@ int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaSt
         const SysEntry *en = reinterpret_cast<const SysEntry *>(base + b.entry_off);
         const uint32_t *pf = reinterpret_cast<const uint32_t *>(base + b.prefix_off);
         uint32_t *ctr = scratch + 2 * i, *err = scratch + 2 * i + 1;
-        cudaStream_t st = (two && (i & 1)) ? aux : stream;
+        const int lane_of = (int)(i % (size_t)(extra + 1));
+        cudaStream_t st = lane_of == 0 ? stream : ss->aux[lane_of - 1];
         switch (b.R) {
 #define GBD_CASE(RR) case RR: rc = affine ? launch_bucket<RR, true>(d_jobs, en, pf, b.nentries, b.nunits, b.piece, ctr, err, sm_count, st) \
                                          : launch_bucket<RR, false>(d_jobs, en, pf, b.nentries, b.nunits, b.piece, ctr, err, sm_count, st); break;
@@ -656,9 +684,9 @@ int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaSt
             default: rc = fail(GBD_EINVAL, "internal: bad rows per lane");
         }
     }
-    if (two) {
-        cudaEventRecord(join, aux);
-        cudaStreamWaitEvent(stream, join, 0);
+    for (int k = 0; k < extra; ++k) {
+        cudaEventRecord(ss->join[k], ss->aux[k]);
+        cudaStreamWaitEvent(stream, ss->join[k], 0);
     }
     cudaError_t fe = cudaFreeAsync(scratch, stream);
     if (rc != GBD_OK) return rc;

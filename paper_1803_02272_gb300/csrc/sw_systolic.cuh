@@ -45,12 +45,13 @@ uint32_t tuned_piece(uint64_t pairs, double mean_len, int warps);
 int systolic_resident_warps(int sm_count);
 void free_plan(SysPlan &plan, cudaStream_t stream);
 
-// aux: optional second stream; consecutive buckets alternate between the two, forking
-// and joining on the events fork / join (owned by the caller; needed when aux is set).
+// ss, naux: consecutive buckets alternate between `stream` and the first naux streams of
+// ss (naux <= StreamSet::kMaxAux; ss == nullptr or naux == 0: one stream).
 // affine: the jobs use affine gaps (every job of the launch the same way).
 int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaStream_t stream,
-                 cudaStream_t aux = nullptr, cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr,
-                 bool affine = false);
+                 const StreamSet *ss = nullptr, int naux = 0, bool affine = false);
+// Streams the plain (non-batched) launches use: the caller's and one more.
+constexpr int kDefaultAuxStreams = 1;
 // Largest gap opening penalty the systolic kernel takes (its int16 values stay in range).
 constexpr int kSystolicMaxGapOpen = 1000;
 size_t systolic_smem_bytes();

@@ -141,9 +141,10 @@ __device__ __forceinline__ void label_join_atomic(int32_t *p, int32_t v)
     }
 }
 
-constexpr uint32_t kRectSegVec = 4096;     // 8-entry vectors per rectangle work unit
+constexpr uint32_t kSegVec = 1024;         // 8-entry vectors per work unit (8,192 entries)
+constexpr int kVecPerLane = 4;             // vectors per lane per iteration
 
-// Where a rectangle's hits go and how its rows are laid out.
+// Where a pass's hits go.
 struct RectOut {
     uint32_t *hits;                 // (row, col, d) triples, or
     uint2 *edges;                   // (row, col) pairs (when set)
@@ -153,21 +154,41 @@ struct RectOut {
     int32_t *row_labels;            // the label of row a0 + rr (pre-set to -1)
 };
 
-// Bookkeeping of one row of a rectangle: entries of row rr start at out + rr*ld + c_lo
-// (c_lo = rr for a triangle band, whose row a0 + rr holds columns b0 + rr ..).  Vectors
-// of 8 entries run from the row's first 16-byte boundary; head entries come before it,
-// tail entries after the last full vector.
+// The rows a pass streams over.  Row rr of the pass is read a0 + rr; its entry for column
+// b0 + c lies at:
+//   SPAN_RECT  out[rr * ld + c], c in [0, nb)
+//   SPAN_BAND  out[rr * ld + c], c in [rr, nb) (row a0 + rr of a triangle band: columns
+//              after the row's own read)
+//   SPAN_TRI   the strict upper triangle of nb reads (a0 = b0 = 0): out[k(rr, c)], c in
+//              [rr + 1, nb)
+enum SpanKind : int { SPAN_RECT = 0, SPAN_BAND = 1, SPAN_TRI = 2 };
+
+struct Spans {
+    const uint16_t *out;
+    uint64_t ld, rows, nb, a0, b0;
+};
+
+// One row of a pass: entries start at p (column b0 + c_lo); vectors of 8 entries run from
+// the row's first 16-byte boundary; head entries come before it, tail entries after the
+// last full vector.
 struct RowSpan {
     const uint16_t *p;
     uint64_t c_lo, head, nvec, tail0, nbr;
 };
 
-__device__ __forceinline__ RowSpan row_span(const uint16_t *out, uint64_t ld, uint64_t rr, uint64_t nb, bool band)
+template <int KIND>
+__device__ __forceinline__ RowSpan row_span(const Spans &S, uint64_t rr)
 {
     RowSpan rs;
-    rs.c_lo = band ? rr : 0;
-    rs.nbr = nb > rs.c_lo ? nb - rs.c_lo : 0;
-    rs.p = out + rr * ld + rs.c_lo;
+    if (KIND == SPAN_TRI) {
+        rs.c_lo = rr + 1;
+        rs.nbr = S.nb - 1 - rr;
+        rs.p = S.out + (rr * S.nb - rr * (rr + 1) / 2);
+    } else {
+        rs.c_lo = KIND == SPAN_BAND ? rr : 0;
+        rs.nbr = S.nb > rs.c_lo ? S.nb - rs.c_lo : 0;
+        rs.p = S.out + rr * S.ld + rs.c_lo;
+    }
     uint64_t head = ((16u - (uint32_t)(reinterpret_cast<uintptr_t>(rs.p) & 15u)) & 15u) / 2u;
     rs.head = head > rs.nbr ? rs.nbr : head;
     rs.nvec = (rs.nbr - rs.head) / 8;
@@ -188,45 +209,75 @@ __device__ __forceinline__ void put_hit(const RectOut &o, unsigned long long slo
     }
 }
 
-// The rectangle as (row, segment) work units strided over the grid, kRectSegVec vectors
-// of a row per segment; segment 0 also takes the row's (fewer than 16) head and tail
-// entries with one warp.  Hits are appended with one atomic per warp; a unit's species
-// view is combined in the block, then joined into the row's label.  Column bounds:
-// TB[toff + c] = hit_bound of column b0 + c (TB 4-byte aligned, toff 0 or 1, readable
-// 10 entries past the last column).
-__global__ void __launch_bounds__(256)
-rect_epilogue_kernel(const uint16_t *__restrict__ out, uint64_t ld, bool band, const uint16_t *__restrict__ lenA,
-                     uint64_t a0, uint64_t a1, const uint16_t *__restrict__ TB, uint32_t toff, uint64_t b0,
-                     uint64_t nb, Threshold th, RectOut o)
+// Smallest of the eight distances of a vector, in both halves of the result's pair of
+// packed minima (the caller takes the smaller half).
+__device__ __forceinline__ uint32_t vmin8(const uint4 &x)
 {
-    __shared__ int32_t lab[8];
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t rows = (uint32_t)(a1 - a0);                  // rows * nseg < 2^32 (host)
-    const uint32_t nseg = (uint32_t)(((nb + 7) / 8 + kRectSegVec - 1) / kRectSegVec);
+    return __vminu2(__vminu2(x.x, x.y), __vminu2(x.z, x.w));
+}
+
+__device__ __forceinline__ uint32_t half_min(uint32_t m) { return min(m & 0xffffu, m >> 16); }
+
+// The rows of a pass as (row, segment) work units of kSegVec vectors, each owned by one
+// warp (units strided over all warps of the grid, segment-major so that the warps of a
+// block work on the same columns and share their bounds in L1; no block-wide
+// synchronisation); the warp of a row's segment 0 also takes the row's (fewer than 16)
+// head and tail entries.  A hit needs d <= max(row bound, column bound) <= thr =
+// max(row bound, tcap), tcap the bound of the longest column read, so a lane takes the
+// minimum of each of its four vectors (packed 16-bit mins) and only vectors whose minimum
+// is at most thr are candidates.  Candidates are appended to a per-warp queue in shared
+// memory (vector and index) and tested against the column bound table 32 at a time, one
+// per lane, so the exact test runs with every lane busy however the candidates are
+// spread; the queue is drained at the end of each unit (its entries share the unit's
+// row).  The four vectors of the next iteration are loaded before the current ones are
+// filtered.  Hits are appended with one atomic per warp; for the annotation, a unit's
+// species view is combined in the warp and joined into the row's label.  Column bounds:
+// TB[toff + c] = hit_bound of column b0 + c (TB 4-byte aligned, toff 0 or 1, readable 10
+// entries past the last column).
+constexpr int kQueue = 64;                 // candidate queue entries per warp (a power of two)
+constexpr int kSpanWarps = 8;              // warps per block
+
+template <int KIND>
+__global__ void __launch_bounds__(kSpanWarps * 32)
+span_epilogue_kernel(Spans S, const uint16_t *__restrict__ lenA, const uint16_t *__restrict__ TB, uint32_t toff,
+                     uint32_t tcap, Threshold th, RectOut o)
+{
+    __shared__ uint4 qx[kSpanWarps][kQueue];
+    __shared__ uint32_t qv[kSpanWarps][kQueue];
+    const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t warp_id = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t maxrow = KIND == SPAN_TRI ? S.nb - 1 : S.nb;      // longest row
+    const uint32_t nseg = (uint32_t)(((maxrow + 7) / 8 + kSegVec - 1) / kSegVec);
+    const uint64_t units = S.rows * nseg;
     const bool want_hits = o.count != nullptr;
     const bool want_labels = o.row_labels != nullptr;
-    for (uint32_t u = blockIdx.x; u < rows * nseg; u += gridDim.x) {
-        const uint32_t rr = u / nseg, seg = u - rr * nseg;
-        const uint64_t r = a0 + rr;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (uint64_t u = warp_id; u < units; u += nwarps) {
+        const uint32_t seg = (uint32_t)(u / S.rows);
+        const uint64_t rr = u - (uint64_t)seg * S.rows;
+        const RowSpan rs = row_span<KIND>(S, rr);
+        const uint32_t v0 = seg * kSegVec;
+        if (seg > 0 && v0 >= rs.nvec) continue;                        // warp-uniform
+        const uint64_t r = S.a0 + rr;
         const uint32_t ti = hit_bound(lenA[r], th);
-        const RowSpan rs = row_span(out, ld, rr, nb, band);
-        const uint64_t cb = b0 + rs.c_lo;            // column of the row's entry 0
+        const uint32_t thr = max(ti, tcap);
+        const uint64_t cb = S.b0 + rs.c_lo;          // column of the row's entry 0
         const uint64_t tb = toff + rs.c_lo;          // its index in TB
         int32_t mine = -1;
-        // vectors of this segment; the loop bound is warp-uniform so all lanes vote
-        const uint32_t v0 = seg * kRectSegVec, v1 = (uint32_t)min(rs.nvec, (uint64_t)v0 + kRectSegVec);
+        const uint32_t v1 = (uint32_t)min(rs.nvec, (uint64_t)v0 + kSegVec);
         const uint4 *pv = reinterpret_cast<const uint4 *>(rs.p + rs.head);
         // TB from an even index at or before the bound of the row's vector 0 (so 32-bit
         // loads stay aligned), and that bound's offset from there
         const uint64_t t0 = tb + rs.head;
         const uint16_t *tbv = TB + (t0 & ~1ull);
         const uint32_t par = (uint32_t)(t0 & 1);
-        // the hits of one lane's vector v (mask hm, data w); called by the whole warp
-        auto take = [&](uint32_t v, const uint32_t w[4], uint32_t hm) {
+        // the hits of one lane's vector v (mask hm, data x); called by the whole warp
+        auto take = [&](uint32_t v, const uint4 &x, uint32_t hm) {
             if (!__any_sync(0xffffffffu, hm != 0)) return;
             const uint64_t c = rs.head + 8 * (uint64_t)v;
             unsigned long long slot = want_hits ? warp_reserve(o.count, __popc(hm)) : 0;
-            const uint64_t lo = (uint64_t)w[1] << 32 | w[0], hi = (uint64_t)w[3] << 32 | w[2];
+            const uint64_t lo = (uint64_t)x.y << 32 | x.x, hi = (uint64_t)x.w << 32 | x.z;
             while (hm) {
                 const int e = __ffs(hm) - 1;
                 hm &= hm - 1;
@@ -239,22 +290,58 @@ rect_epilogue_kernel(const uint16_t *__restrict__ out, uint64_t ld, bool band, c
                 }
             }
         };
-        // two vectors per lane per iteration (v and v + 32), both loads issued first
-        for (uint32_t vb = v0 + warp * 64; vb < v1; vb += 2 * blockDim.x) {
-            const uint32_t va = vb + lane, vc = vb + 32 + lane;
-            const bool oka = va < v1, okc = vc < v1;
-            uint4 xa = make_uint4(0u, 0u, 0u, 0u), xc = make_uint4(0u, 0u, 0u, 0u);
-            if (oka) xa = __ldg(pv + va);
-            if (okc) xc = __ldg(pv + vc);
-            const uint32_t wa[4] = {xa.x, xa.y, xa.z, xa.w}, wc[4] = {xc.x, xc.y, xc.z, xc.w};
-            const uint32_t ha = oka ? hits8(wa, ti, tbv, 8 * va + par) : 0u;
-            const uint32_t hc = okc ? hits8(wc, ti, tbv, 8 * vc + par) : 0u;
-            if (!__any_sync(0xffffffffu, (ha | hc) != 0)) continue;
-            take(va, wa, ha);
-            take(vc, wc, hc);
+        // the queue: entries [qhead, qtail) (indices mod kQueue), fewer than 32 between batches
+        uint32_t qhead = 0, qtail = 0;
+        auto test_batch = [&](uint32_t cnt) {        // the oldest cnt (<= 32) queued candidates
+            uint32_t hm = 0, v = 0;
+            uint4 x = make_uint4(0u, 0u, 0u, 0u);
+            if (lane < cnt) {
+                const uint32_t slot = (qhead + lane) & (kQueue - 1);
+                x = qx[wib][slot];
+                v = qv[wib][slot];
+                const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+                hm = hits8(w, ti, tbv, 8 * (uint64_t)v + par);
+            }
+            take(v, x, hm);
+            qhead += cnt;
+        };
+        constexpr uint32_t kStep = 32 * kVecPerLane;
+        auto load = [&](uint32_t vb, uint4 (&x)[kVecPerLane]) {
+#pragma unroll
+            for (int k = 0; k < kVecPerLane; ++k) {
+                const uint32_t v = vb + 32 * k + lane;
+                x[k] = v < v1 ? __ldg(pv + v) : make_uint4(~0u, ~0u, ~0u, ~0u);
+            }
+        };
+        uint4 nx[kVecPerLane];
+        load(v0, nx);
+        for (uint32_t vb = v0; vb < v1; vb += kStep) {
+            uint4 x[kVecPerLane];
+#pragma unroll
+            for (int k = 0; k < kVecPerLane; ++k) x[k] = nx[k];
+            if (vb + kStep < v1) load(vb + kStep, nx);             // next iteration's loads first
+#pragma unroll
+            for (int k = 0; k < kVecPerLane; ++k) {
+                const uint32_t v = vb + 32 * k + lane;
+                const bool cand = v < v1 && half_min(vmin8(x[k])) <= thr;
+                const uint32_t cm = __ballot_sync(0xffffffffu, cand);
+                if (cm == 0) continue;
+                if (cand) {
+                    const uint32_t slot = (qtail + __popc(cm & lt_mask)) & (kQueue - 1);
+                    qx[wib][slot] = x[k];
+                    qv[wib][slot] = v;
+                }
+                qtail += __popc(cm);
+                __syncwarp();
+                if (qtail - qhead >= 32) {
+                    test_batch(32);
+                    __syncwarp();
+                }
+            }
         }
-        // entries before the first boundary and after the last vector: warp 0 of segment 0
-        if (seg == 0 && warp == 0) {
+        if (qtail != qhead) test_batch(qtail - qhead);
+        // entries before the first boundary and after the last vector: the warp of segment 0
+        if (seg == 0) {
             const uint64_t ntail = rs.nbr - rs.tail0;
             uint32_t hit = 0, d = 0;
             uint64_t c = 0;
@@ -277,19 +364,13 @@ rect_epilogue_kernel(const uint16_t *__restrict__ out, uint64_t ld, bool band, c
         if (want_labels) {
 #pragma unroll
             for (int k = 16; k > 0; k >>= 1) mine = label_join(mine, __shfl_xor_sync(0xffffffffu, mine, k));
-            if (lane == 0) lab[warp] = mine;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int32_t x = -1;
-                for (uint32_t k = 0; k < blockDim.x / 32; ++k) x = label_join(x, lab[k]);
-                label_join_atomic(o.row_labels + rr, x);
-            }
-            __syncthreads();
+            if (lane == 0) label_join_atomic(o.row_labels + rr, mine);
         }
+        __syncwarp();
     }
 }
 
-// Direct unions over a triangle band (layout as in rect_epilogue_kernel with band set),
+// Direct unions over a triangle band (layout SPAN_BAND of span_epilogue_kernel),
 // one block per row; runs only when the band's edge list overflowed (*count > cap).
 __global__ void __launch_bounds__(256)
 band_union_rows_kernel(const uint16_t *__restrict__ out, uint64_t ld, const uint16_t *__restrict__ T,
@@ -340,109 +421,6 @@ tri_union_kernel(const uint16_t *__restrict__ tri, const uint16_t *__restrict__ 
     if (count) {
         for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
         if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
-    }
-}
-
-__device__ __forceinline__ uint64_t tri_row_start(uint64_t i, uint64_t n) { return i * n - i * (i + 1) / 2; }
-
-// (i, j) of flat triangle index k (row-major strict upper triangle of n reads).
-__device__ __forceinline__ void tri_unindex(uint64_t k, uint64_t n, uint64_t &i, uint64_t &j)
-{
-    const double b = 2.0 * (double)n - 1.0;
-    int64_t r = (int64_t)((b - sqrt(fmax(b * b - 8.0 * (double)k, 0.0))) * 0.5);
-    if (r < 0) r = 0;
-    if (r > (int64_t)n - 2) r = (int64_t)n - 2;
-    while (r + 1 <= (int64_t)n - 2 && tri_row_start((uint64_t)r + 1, n) <= k) ++r;
-    while (r > 0 && tri_row_start((uint64_t)r, n) > k) --r;
-    i = (uint64_t)r;
-    j = k - tri_row_start(i, n) + i + 1;
-}
-
-// The triangle as one flat stream: each warp owns a contiguous run of 256-entry spans
-// and lane l reads entries 8l .. 8l+7 of a span with one 16-byte load (the triangle must
-// be 16-byte aligned), the next span's load issued before the current span is tested.
-// A lane whose eight entries lie in one row tests them against the bound table T with
-// any_hit8; a lane across a row end, or at the triangle's partial end, is a candidate
-// too.  Only when some lane is a candidate does the warp work out exact hit masks (entry
-// by entry, following the rows) and append the hits to an edge list with one atomic.
-// The unions run afterwards one edge per thread, so a warp whose rows are full of hits
-// does not serialise the latency of its unions.  Every hit is counted; edges past the
-// list's capacity are left to tri_union_rows_kernel.  Row and column indices are 32-bit
-// (n < 2^32).
-__global__ void __launch_bounds__(256)
-tri_hits_stream_kernel(const uint16_t *__restrict__ tri, const uint16_t *__restrict__ T, uint32_t n,
-                       uint64_t m, uint2 *edges, uint64_t cap, unsigned long long *count)
-{
-    const uint64_t warp_id = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint32_t lane = threadIdx.x & 31;
-    const uint64_t spans = (m + 255) / 256;
-    const uint64_t per = (spans + nwarps - 1) / nwarps;
-    const uint64_t s0 = warp_id * per, s1 = min(spans, s0 + per);
-    if (s0 >= s1) return;                      // warp-uniform
-    const uint64_t full_end = min(s1, m / 256);   // spans [s0, full_end) hold 256 entries
-    uint32_t i = 0, j = 1;
-    const uint64_t k_first = s0 * 256 + 8 * lane;
-    if (k_first < m) {
-        uint64_t ii, jj;
-        tri_unindex(k_first, n, ii, jj);
-        i = (uint32_t)ii;
-        j = (uint32_t)jj;
-    }
-    const uint4 *p = reinterpret_cast<const uint4 *>(tri) + s0 * 32 + lane;
-    uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
-    if (s0 < full_end) nxt = __ldg(p);
-    for (uint64_t sp = s0; sp < s1; ++sp) {
-        uint32_t w[4] = {nxt.x, nxt.y, nxt.z, nxt.w};
-        p += 32;
-        if (sp + 1 < full_end) nxt = __ldg(p);
-        const bool full = sp < full_end;
-        // slow: the triangle's partial last span, or entries that cross a row end
-        bool slow;
-        uint32_t hm = 0;
-        if (!full) slow = sp * 256 + 8 * lane < m;
-        else if ((uint64_t)j + 7 >= n) slow = true;
-        else { slow = false; hm = hits8(w, T[i], T, j); }
-        if (__any_sync(0xffffffffu, slow || hm != 0)) {
-            const uint64_t kb = sp * 256 + 8 * lane;
-            if (slow) {
-                // entries e < 4 in lo, the rest in hi (64-bit shifts keep w in registers)
-                uint64_t lo = (uint64_t)w[1] << 32 | w[0], hi = (uint64_t)w[3] << 32 | w[2];
-                if (!full) {                   // the triangle's last, partial vector
-                    lo = hi = 0;
-                    for (uint64_t e = 0; kb + e < m; ++e) {
-                        const uint64_t v = tri[kb + e];
-                        if (e < 4) lo |= v << (16 * e);
-                        else hi |= v << (16 * (e - 4));
-                    }
-                }
-                uint32_t ii = i, jj = j, ti = T[i];
-                for (int e = 0; e < 8 && kb + e < m; ++e) {
-                    const uint32_t d = (uint32_t)(((e < 4) ? lo : hi) >> (16 * (e & 3))) & 0xffffu;
-                    if (d <= max(ti, (uint32_t)T[jj])) hm |= 1u << e;
-                    if (++jj == n) { ++ii; jj = ii + 1; ti = T[ii]; }
-                }
-            }
-            if (__any_sync(0xffffffffu, hm != 0)) {
-                unsigned long long slot = warp_reserve(count, __popc(hm));
-                uint32_t ii = i, jj = j;
-                for (int e = 0; e < 8 && hm; ++e) {
-                    if ((hm >> e) & 1u) {
-                        if (slot < cap) edges[slot] = make_uint2(ii, jj);
-                        ++slot;
-                        hm &= ~(1u << e);
-                    }
-                    if (++jj == n) { ++ii; jj = ii + 1; }
-                }
-            }
-        }
-        // advance by one span (256 entries), across row ends
-        j += 256;
-        while (j >= n && i + 2 < n) {
-            const uint32_t over = j - n;
-            ++i;
-            j = i + 1 + over;
-        }
     }
 }
 
@@ -532,21 +510,35 @@ int check_launch(const char *what)
 
 }  // namespace
 
-// The rectangle kernel counts work units and a row's vectors in 32 bits.
-static bool rect_units_fit(uint64_t rows, uint64_t nb)
+// The span kernel counts a row's vectors in 32 bits.
+static bool span_units_fit(uint64_t rows, uint64_t maxrow)
 {
-    const uint64_t nseg = ((nb + 7) / 8 + kRectSegVec - 1) / kRectSegVec;
-    return nb / 8 < (1ull << 32) && rows * nseg < (1ull << 32);
+    (void)rows;
+    return maxrow / 8 < (1ull << 32) - kSegVec;
+}
+
+// Blocks of 256 threads (8 warps, one work unit each at a time) for a pass.
+static uint64_t span_units(uint64_t rows, uint64_t maxrow)
+{
+    return (rows * (((maxrow + 7) / 8 + kSegVec - 1) / kSegVec) + 7) / 8;
+}
+
+// hit_bound on the host: the bound of the longest column read caps every column bound.
+static uint32_t host_hit_bound(uint32_t len, const Threshold &th)
+{
+    uint64_t q = (uint64_t)th.num * len / th.den;
+    if (q > th.abs_max) q = th.abs_max;
+    return q > 65535u ? 65535u : (uint32_t)q;
 }
 
 int launch_rect_epilogue(const uint16_t *out, uint64_t ld, const DeviceReads &A, uint64_t a0, uint64_t a1,
-                         const DeviceReads &B, uint64_t b0, uint64_t b1, const Threshold &th, uint32_t *hits,
-                         uint64_t cap, unsigned long long *count, const int32_t *col_labels,
+                         const DeviceReads &B, uint64_t b0, uint64_t b1, uint32_t colmax_len, const Threshold &th,
+                         uint32_t *hits, uint64_t cap, unsigned long long *count, const int32_t *col_labels,
                          int32_t *row_labels, int sm_count, cudaStream_t st)
 {
     if (a1 <= a0 || b1 <= b0) return GBD_OK;
     if (!count && !(row_labels && col_labels)) return GBD_OK;
-    if (!rect_units_fit(a1 - a0, b1 - b0)) return fail(GBD_EINVAL, "rectangle too large for one epilogue pass");
+    if (!span_units_fit(a1 - a0, b1 - b0)) return fail(GBD_EINVAL, "rectangle too large for one epilogue pass");
     // bounds of columns b0 - toff .. b1 - 1 (toff makes the table's first word hold an
     // even column, so its 32-bit loads are aligned), zero padding after
     const uint64_t nb = b1 - b0;
@@ -558,12 +550,12 @@ int launch_rect_epilogue(const uint16_t *out, uint64_t ld, const DeviceReads &A,
                                                                                   TB);
     int rc = check_launch("hit_bound_kernel launch");
     if (rc == GBD_OK) {
-        const uint64_t nseg = ((nb + 7) / 8 + kRectSegVec - 1) / kRectSegVec;
         const RectOut o{hits, nullptr, cap, count, col_labels, row_labels && col_labels ? row_labels : nullptr};
-        rect_epilogue_kernel<<<resident_grid(rect_epilogue_kernel, sm_count, (a1 - a0) * nseg), 256, 0, st>>>(
-            out, ld, false, A.len, a0, a1,
-                                                                                      TB, toff, b0, nb, th, o);
-        rc = check_launch("rect_epilogue_kernel launch");
+        const Spans S{out, ld, a1 - a0, nb, a0, b0};
+        span_epilogue_kernel<SPAN_RECT>
+            <<<resident_grid(span_epilogue_kernel<SPAN_RECT>, sm_count, span_units(a1 - a0, nb)), 256, 0, st>>>(
+                S, A.len, TB, toff, host_hit_bound(colmax_len, th), th, o);
+        rc = check_launch("span_epilogue_kernel launch");
     }
     cudaFreeAsync(TB, st);
     return rc;
@@ -587,19 +579,19 @@ int band_forest_begin(BandForest &bf, const DeviceReads &S, const Threshold &th,
 }
 
 int band_forest_add(BandForest &bf, const uint16_t *rect, uint64_t ld, const DeviceReads &S, uint64_t a0, uint64_t a1,
-                    const Threshold &th, uint32_t *parent, int sm_count, cudaStream_t st)
+                    uint32_t max_len, const Threshold &th, uint32_t *parent, int sm_count, cudaStream_t st)
 {
     const uint64_t n = S.n;
     if (a1 <= a0 || a0 + 1 >= n) return GBD_OK;
     const uint64_t b0 = a0 + 1, nb = n - b0;
-    if (!rect_units_fit(a1 - a0, nb)) return fail(GBD_EINVAL, "band too large for one epilogue pass");
+    if (!span_units_fit(a1 - a0, nb)) return fail(GBD_EINVAL, "band too large for one epilogue pass");
     const uint32_t toff = (uint32_t)(b0 & 1);
-    const uint64_t nseg = ((nb + 7) / 8 + kRectSegVec - 1) / kRectSegVec;
     const RectOut o{nullptr, bf.edges, bf.cap, bf.cnt, nullptr, nullptr};
-    rect_epilogue_kernel<<<resident_grid(rect_epilogue_kernel, sm_count, (a1 - a0) * nseg), 256, 0, st>>>(
-        rect, ld, true, S.len, a0, a1,
-                                                                                  bf.T + (b0 - toff), toff, b0, nb, th, o);
-    int rc = check_launch("rect_epilogue_kernel launch");
+    const Spans Sp{rect, ld, a1 - a0, nb, a0, b0};
+    span_epilogue_kernel<SPAN_BAND>
+        <<<resident_grid(span_epilogue_kernel<SPAN_BAND>, sm_count, span_units(a1 - a0, nb)), 256, 0, st>>>(
+            Sp, S.len, bf.T + (b0 - toff), toff, host_hit_bound(max_len, th), th, o);
+    int rc = check_launch("span_epilogue_kernel launch");
     const int eg = grid_of((bf.cap + 255) / 256, sm_count, 16);
     if (rc == GBD_OK) {
         if (bf.first) min_hook_kernel<true><<<eg, 256, 0, st>>>(bf.edges, bf.cap, bf.cnt, parent);
@@ -643,8 +635,8 @@ int band_forest_end(BandForest &bf, uint32_t *parent, uint64_t n, unsigned long 
     return rc;
 }
 
-int launch_tri_components(const uint16_t *tri, const DeviceReads &S, const Threshold &th, uint32_t *parent,
-                          unsigned long long *count, int sm_count, cudaStream_t st)
+int launch_tri_components(const uint16_t *tri, const DeviceReads &S, uint32_t max_len, const Threshold &th,
+                          uint32_t *parent, unsigned long long *count, int sm_count, cudaStream_t st)
 {
     const uint64_t n = S.n;
     iota_kernel<<<grid_of((n + 255) / 256, sm_count, 16), 256, 0, st>>>(parent, n);
@@ -652,7 +644,7 @@ int launch_tri_components(const uint16_t *tri, const DeviceReads &S, const Thres
     if (rc != GBD_OK) return rc;
     if (n >= 2) {
         const uint64_t m = n * (n - 1) / 2;
-        if (reinterpret_cast<uintptr_t>(tri) % 16 == 0) {
+        if (reinterpret_cast<uintptr_t>(tri) % 2 == 0 && span_units_fit(n - 1, n - 1)) {
             // edge list of up to kEdgeCap hits, then one union per edge; the row kernel
             // takes over only if the list overflowed
             const uint64_t cap = std::min<uint64_t>(m, kEdgeCap);
@@ -666,10 +658,12 @@ int launch_tri_components(const uint16_t *tri, const DeviceReads &S, const Thres
             hit_bound_kernel<<<grid_of((n + 16 + 255) / 256, sm_count, 8), 256, 0, st>>>(S.len, n, n + 16, th, T);
             rc = check_launch("hit_bound_kernel launch");
             if (rc == GBD_OK) {
-                tri_hits_stream_kernel<<<resident_grid(tri_hits_stream_kernel, sm_count, (m + 255) / 256), 256, 0, st>>>(
-                    tri, T, (uint32_t)n, m,
-                                                                                               edges, cap, cnt);
-                rc = check_launch("tri_hits_stream_kernel launch");
+                const RectOut o{nullptr, edges, cap, cnt, nullptr, nullptr};
+                const Spans Sp{tri, 0, n - 1, n, 0, 0};
+                span_epilogue_kernel<SPAN_TRI>
+                    <<<resident_grid(span_epilogue_kernel<SPAN_TRI>, sm_count, span_units(n - 1, n - 1)), 256, 0, st>>>(
+                        Sp, S.len, T, 0, host_hit_bound(max_len, th), th, o);
+                rc = check_launch("span_epilogue_kernel launch");
             }
             cudaFreeAsync(T, st);
             if (rc == GBD_OK) {

@@ -92,7 +92,8 @@ def _declare(lib):
         "gbd_rect_hits": ([vp, vp, u64, u64, vp, u64, u64, vp, u64, ctypes.POINTER(GbdThreshold), vp, u64,
                            vp, vp, vp, vp], ci),
         "gbd_tri_components": ([vp, vp, vp, ctypes.POINTER(GbdThreshold), vp, vp, vp], ci),
-        "gbd_batch_tuning": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+        "gbd_batch_tuning": ([vp, u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_int32),
                               ctypes.POINTER(ci)], ci),
     }
     for name, (args, res) in sig.items():
@@ -205,12 +206,20 @@ def gbd_batch(ctx: int, samples, d_tris, stream=None) -> None:
 
 
 def gbd_batch_tuning(ctx: int) -> dict:
-    """Autotuner state of the context's batched launch."""
-    ms = (ctypes.c_double * 3)()
-    sc = ctypes.c_double()
+    """Autotuner state of the context's batched launch: per candidate its time (ms), work-unit
+    scale and stream count, the chosen candidate (-1 while tuning) and whether tuning is done."""
+    cap = 16
+    ms = (ctypes.c_double * cap)()
+    sc = (ctypes.c_double * cap)()
+    streams = (ctypes.c_int32 * cap)()
+    nt = ctypes.c_uint32()
+    chosen = ctypes.c_int32()
     done = ctypes.c_int()
-    _check(_lib.gbd_batch_tuning(ctx, ms, ctypes.byref(sc), ctypes.byref(done)))
-    return {"trial_ms": list(ms), "piece_scale": sc.value, "done": bool(done.value)}
+    _check(_lib.gbd_batch_tuning(ctx, cap, ms, sc, streams, ctypes.byref(nt), ctypes.byref(chosen),
+                                 ctypes.byref(done)))
+    k = nt.value
+    return {"trial_ms": list(ms)[:k], "piece_scale": list(sc)[:k], "streams": list(streams)[:k],
+            "chosen": chosen.value, "done": bool(done.value)}
 
 
 def gbd_server_create(ctx: int, ref: int) -> int:

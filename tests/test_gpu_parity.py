@@ -204,8 +204,9 @@ def test_batch_matches_per_sample(gbd):
 
 
 def test_batch_autotuner(gbd):
-    """The first calls time three work-unit sizes, then the fastest is kept; every call's
-    output is exact."""
+    """The first five calls time one candidate each (work-unit scales 1, 0.5, 2 with two
+    streams, then the best scale with one and three streams), then the fastest is kept;
+    every call's output is exact."""
     import torch
     samples = synth.workload_batched(n_samples=6, n_lo=50, n_hi=400)
     ctx = _ctx(gbd)
@@ -213,7 +214,7 @@ def test_batch_autotuner(gbd):
     outs = [torch.empty(max(s.n * (s.n - 1) // 2, 1), dtype=torch.int16, device="cuda") for s in samples]
     want = [oracle.all_pairs(rs) for rs in samples]
     states = []
-    for call in range(6):
+    for call in range(8):
         for o in outs:
             o.fill_(-1)
         ctx.batch(sets, outs=outs)
@@ -221,10 +222,15 @@ def test_batch_autotuner(gbd):
         for rs, o, w in zip(samples, outs, want):
             np.testing.assert_array_equal(gbd.as_uint16(o[: rs.n * (rs.n - 1) // 2]), w)
         states.append(gbd.gbd_batch_tuning(ctx.handle))
-    assert not states[0]["done"] and states[3]["done"] and states[5]["done"]
-    t = states[5]["trial_ms"]
-    assert all(x > 0 for x in t)
-    assert states[5]["piece_scale"] == [1.0, 0.5, 2.0][int(np.argmin(t))]
+    assert not states[0]["done"] and not states[4]["done"] and states[5]["done"] and states[7]["done"]
+    assert states[0]["chosen"] == -1
+    st = states[7]
+    t = st["trial_ms"]
+    assert len(t) == 5 and all(x > 0 for x in t)
+    assert st["piece_scale"][:3] == [1.0, 0.5, 2.0] and st["streams"] == [2, 2, 2, 1, 3]
+    best_scale = [1.0, 0.5, 2.0][int(np.argmin(t[:3]))]
+    assert st["piece_scale"][3] == st["piece_scale"][4] == best_scale
+    assert st["chosen"] == int(np.argmin(t))
 
 
 def test_batch_graph_replay_and_recapture(gbd):
