@@ -13,6 +13,14 @@ uint16 distances, ~10 GB, larger than L2).  The metric is GCUPS: DP cells
 Under torchrun each rank runs an independent replica of the workload on its own GPU
 (the path is computed on one GPU; there is no data-path collective), the time is the
 maximum over ranks, and value counts the cells of every rank.
+
+Besides the timed steps, rank 0 measures: the end-to-end figure (the last warm-up step,
+run through host buffers), the oracle on a bounded sample of the same pairs (the
+cpu_baseline, whose sample is grown to 2e6 pairs to check the timed triangle), and, while
+the --time-budget allows, the batched form against per-sample launches (64 uneven
+samples), the served form against per-request launches (a burst of requests against the
+resident 1e5-read set), and the served-batch latency under Poisson arrivals.  The run
+exits 1 when a checked distance differs from the oracle's.
 """
 from __future__ import annotations
 
@@ -30,6 +38,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+T_START = time.perf_counter()        # the time guard of the optional phases counts from here
 METRIC = "GCUPS, all-pairs n=1e5 (bit-exact)"
 UNIT = "GCUPS"
 L2_FLUSH_BYTES = 512 << 20
@@ -52,8 +61,15 @@ def parse_args(argv=None):
                     help="uniformly sampled pairs of the timed triangle compared with the oracle")
     ap.add_argument("--mode", choices=["allpairs", "batch", "serve", "mds", "components", "affine", "annotate"],
                     default="allpairs")
-    ap.add_argument("--serve-requests", type=int, default=40,
-                    help="requests in the serving phase of the all-pairs run (0 = skip)")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests in the serving phase of the all-pairs run (0 = skip); fewer (at "
+                         "least 40) when the time budget leaves less room")
+    ap.add_argument("--time-budget", type=float, default=1700.0,
+                    help="seconds from start within which the all-pairs run schedules its optional "
+                         "phases (batched and served comparisons, serving latency)")
+    ap.add_argument("--no-batch", action="store_true", help="all-pairs run: skip the batched comparison")
+    ap.add_argument("--compare-requests", type=int, default=24,
+                    help="requests of the served-vs-plain burst comparison (0 = skip)")
     ap.add_argument("--serve-load", type=float, default=0.8,
                     help="offered load of that phase, as a fraction of measured pairs/s")
     ap.add_argument("--samples", type=int, default=64, help="batch mode: samples")
@@ -227,6 +243,42 @@ def cpu_baseline_pairs(qs, i, j, ref=None, got=None, gap_open: int = 0, what: st
         got = np.asarray(got, dtype=np.uint16)
         out["check"] = {"pairs_checked": int(len(i)), "mismatches": int(np.count_nonzero(got != want))}
     return out
+
+
+def cpu_baseline_batch(samples, got_fn, all_pairs_upto: int = 600, per_sample: int = 3000, seed: int = 44):
+    """The oracle on the batched workload: every pair of the samples of at most
+    all_pairs_upto reads, per_sample uniformly drawn pairs of each larger one; compared with
+    the GPU's triangles (got_fn(s, i, j) -> distances of sample s)."""
+    import oracle
+    cores = _oracle_cores()
+    rng = np.random.default_rng(seed)
+    checked = mism = 0
+    cells = 0.0
+    t0 = time.perf_counter()
+    n_all = 0
+    for s, rs in enumerate(samples):
+        n = rs.n
+        if n < 2:
+            continue
+        if n <= all_pairs_upto:
+            i, j = np.triu_indices(n, 1)
+            n_all += 1
+        else:
+            i = rng.integers(0, n - 1, size=per_sample)
+            j = i + 1 + (rng.random(per_sample) * (n - 1 - i)).astype(np.int64)
+        i = i.astype(np.int64)
+        j = j.astype(np.int64)
+        want = oracle.pairs(rs, i, j, nthreads=cores)
+        got = np.asarray(got_fn(s, i, j), dtype=np.uint16)
+        checked += len(i)
+        mism += int(np.count_nonzero(got != want))
+        L = rs.lengths.astype(np.float64)
+        cells += float(np.sum(L[i] * L[j]))
+    dt = max(time.perf_counter() - t0, 1e-9)
+    return {"value": cells / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"all pairs of the {n_all} samples of <= {all_pairs_upto} reads, {per_sample} uniformly "
+                      f"drawn pairs of each other sample: {checked} pairs, {dt:.1f} s on {cores} host threads",
+            "check": {"pairs_checked": checked, "mismatches": mism}}
 
 
 def cpu_baseline_components(rs, i, j, th, labels):
@@ -416,8 +468,15 @@ def run_gbd(args):
             ev[1].record(stream)
         return s
 
-    for _ in range(args.warmup):
-        gbd.gbd_free_set(step())
+    # the last warm-up step is the end-to-end one: the same step through host buffers (reads
+    # copied in from pinned host memory, the triangle copied back), timed as e2e
+    e2e = None
+    for w in range(args.warmup):
+        if w == args.warmup - 1 and not args.no_e2e and rank == 0:
+            e2e = run_e2e(gbd, ctx, rs, dev, stream)
+            e2e["note"] = "measured on the last warm-up step"
+        else:
+            gbd.gbd_free_set(step())
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
@@ -479,10 +538,10 @@ def run_gbd(args):
             "triangle_write": triangle_write(m, kern_s),
             "clocks": clocks, "gpu_launches": int(launches), "spot_check": None,
         }
-    if not args.no_e2e and rank == 0:
-        line["e2e"] = run_e2e(gbd, ctx, rs, dev, stream)
-    elif rank == 0:
-        line["e2e"] = None
+    if rank == 0:
+        if e2e is None and not args.no_e2e:
+            e2e = run_e2e(gbd, ctx, rs, dev, stream)
+        line["e2e"] = e2e
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             # the oracle's sample doubles as an exactness check of this very triangle
@@ -498,12 +557,10 @@ def run_gbd(args):
                                      what="uniformly sampled pairs (exactness check only, untimed)")
             line["spot_check"] = chk.pop("check")
         line["exact"] = line["spot_check"]["mismatches"] == 0
-    if args.serve_requests > 0 and rank == 0:
-        # served-batch latency: Poisson arrivals against this set, resident
-        ref = ctx.load(rs)
-        line["serving"] = serve_phase(gbd, ctx, ref, rs, dev, args.serve_requests,
-                                      load=args.serve_load, capacity_pps=pairs_per_s)
-        del ref
+    if rank == 0:
+        del tri
+        line.update(optional_phases(args, gbd, ctx, rs, dev, pairs_per_s, gcups))
+        line["wall_s"] = time.perf_counter() - T_START
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(world)
@@ -512,6 +569,59 @@ def run_gbd(args):
               "checked distances differ from the oracle", file=sys.stderr)
         return 1
     return 0
+
+
+def optional_phases(args, gbd, ctx, rs, dev, pairs_per_s: float, gcups: float) -> dict:
+    """After the timed all-pairs steps: the batched comparison (64 uneven samples), the
+    served-vs-plain comparison (a burst of requests against the resident paper-scale set)
+    and the served-batch latency (Poisson arrivals), in that order.  Each runs only when
+    its duration, estimated from the rates measured so far, fits what is left of
+    --time-budget; the serving phase takes fewer requests (at least 40) to fit."""
+    from paper_1803_02272_gb300 import synth
+    out = {}
+
+    def left():
+        return args.time_budget - (time.perf_counter() - T_START)
+
+    if not args.no_batch:
+        samples = synth.workload_batched(n_samples=args.samples)
+        t_call = sum(x.total_cells() for x in samples) / (gcups * 1e9)
+        est = 2 * 1.1 * t_call + 6 * t_call + 40          # plain 1 + 1, batched 5 + 1, loads and check
+        if est < left():
+            out["batch"] = batch_phase(gbd, ctx, samples, dev, 1, check=not args.no_cpu_baseline)
+        else:
+            out["batch"] = {"skipped": f"time budget: needs about {est:.0f} s, {left():.0f} s left"}
+        del samples
+    ref = ctx.load(rs) if (args.compare_requests > 0 or args.serve_requests > 0) else None
+    capacity = pairs_per_s
+    if args.compare_requests > 0:
+        reqs = synth.workload_served_queries(args.compare_requests, 1.0, seed=1006)
+        est = 2 * sum(r.reads.n for r in reqs) * rs.n / pairs_per_s + 20
+        if est < left():
+            out["serve_vs_plain"] = serve_compare(gbd, ctx, ref, rs, dev, args.compare_requests, seed=1006)
+            capacity = out["serve_vs_plain"]["server_burst"]["pairs_per_s"]
+        else:
+            out["serve_vs_plain"] = {"skipped": f"time budget: needs about {est:.0f} s, {left():.0f} s left"}
+    if args.serve_requests > 0:
+        n_req, est = args.serve_requests, None
+        while True:
+            reqs = synth.workload_served_queries(n_req, 1.0, seed=1005)
+            sizes = [r.reads.n for r in reqs]
+            # Poisson arrivals: the last one comes about 1 +- 1/sqrt(n) of the mean span late
+            est = (1.0 + 2.0 / np.sqrt(n_req)) * sum(sizes) * rs.n / (args.serve_load * capacity) + \
+                max(sizes) * rs.n / capacity + 15
+            if est < left() or n_req <= 40:
+                break
+            n_req = max(40, n_req - 40)
+        if est < left():
+            out["serving"] = serve_phase(gbd, ctx, ref, rs, dev, n_req, load=args.serve_load, capacity_pps=capacity,
+                                         seed=1005)
+            out["serving"]["capacity_basis"] = ("server burst pairs/s of serve_vs_plain" if "server_burst" in
+                                                out.get("serve_vs_plain", {}) else "all-pairs pairs/s")
+        else:
+            out["serving"] = {"skipped": f"time budget: needs about {est:.0f} s, {left():.0f} s left"}
+    del ref
+    return out
 
 
 def run_e2e(gbd, ctx, rs, dev, stream):
@@ -605,14 +715,12 @@ def serve_phase(gbd, ctx, ref_handle, ref_rs, dev, n_requests, load=1.0, capacit
             "spot_check_mismatches": mism, "cpu_baseline": base}
 
 
-def run_batch_mode(args):
-    """64 uneven samples: one gbd_batch call against one gbd_all_pairs call per sample."""
+def batch_phase(gbd, ctx, samples, dev, steps: int, check: bool = True):
+    """The batched workload: one gbd_batch call against one gbd_all_pairs call per sample,
+    timed after warm-up (the batch autotuner's five timed candidates and its pick run as
+    warm-up calls); outputs compared with each other in full and with the oracle on a
+    sample (the cpu_baseline leg)."""
     import torch
-    from paper_1803_02272_gb300 import gbd, synth
-    dev = torch.device("cuda:0")
-    torch.cuda.set_device(0)
-    samples = synth.workload_batched(n_samples=args.samples)
-    ctx = gbd.Context(0)
     sets = [ctx.load(s) for s in samples]
     outs_b = [torch.empty(max(s.n * (s.n - 1) // 2, 1), dtype=torch.int16, device=dev) for s in samples]
     outs_p = [torch.empty_like(o) for o in outs_b]
@@ -627,12 +735,12 @@ def run_batch_mode(args):
         ctx.batch(sets, outs=outs_b)
 
     res = {}
-    for name, fn in (("plain_per_sample", plain), ("batched", batched)):
-        for _ in range(4):                     # warm-up: schedules, and the batch autotuner's
-            fn()                               # three timed candidates plus its pick
+    for name, fn, warm in (("plain_per_sample", plain, 1), ("batched", batched, 5)):
+        for _ in range(warm):                  # batched: the autotuner's five timed candidates;
+            fn()                               # the first timed call records and runs its pick
         torch.cuda.synchronize()
         ts = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             t0 = time.perf_counter()
             fn()
             torch.cuda.synchronize()
@@ -641,12 +749,56 @@ def run_batch_mode(args):
         res[name] = {"seconds": t, "pairs_per_s": pairs / t, "gcups": cells / t / 1e9}
     same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_p))
     tuning = gbd.gbd_batch_tuning(ctx.handle)
-    line = {"mode": "batch", "autotuner": tuning, "workload": f"{len(samples)} samples, read counts "
-            f"{min(s.n for s in samples)}-{max(s.n for s in samples)}, lengths U[150,500]",
-            "pairs": pairs, "cells": cells, "identical_outputs": bool(same), **res,
-            "speedup": res["plain_per_sample"]["seconds"] / res["batched"]["seconds"]}
+    out = {"workload": f"{len(samples)} samples, read counts {min(s.n for s in samples)}-"
+                       f"{max(s.n for s in samples)}, lengths U[150,500]",
+           "pairs": pairs, "cells": cells, "identical_outputs": bool(same), **res,
+           "speedup": res["plain_per_sample"]["seconds"] / res["batched"]["seconds"], "autotuner": tuning}
+    if check:
+        def got(s, i, j):
+            idx = i * samples[s].n - i * (i + 1) // 2 + (j - i - 1)
+            return outs_b[s][torch.from_numpy(idx).to(dev)].cpu().numpy().view(np.uint16)
+        base = cpu_baseline_batch(samples, got)
+        out["spot_check"] = base.pop("check")
+        out["cpu_baseline"] = base
+    del outs_b, outs_p, sets
+    return out
+
+
+def run_batch_mode(args):
+    """64 uneven samples: one gbd_batch call against one gbd_all_pairs call per sample."""
+    import torch
+    from paper_1803_02272_gb300 import gbd, synth
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    samples = synth.workload_batched(n_samples=args.samples)
+    ctx = gbd.Context(0)
+    line = {"mode": "batch", **batch_phase(gbd, ctx, samples, dev, args.steps, check=not args.no_cpu_baseline)}
     print(json.dumps(line), flush=True)
-    return 0
+    return 0 if line.get("spot_check", {"mismatches": 0})["mismatches"] == 0 and line["identical_outputs"] else 1
+
+
+def serve_compare(gbd, ctx, ref, ref_rs, dev, n_requests: int, seed: int = 1006, nq_hi: int = 4096):
+    """Served against plain: the same requests as one gbd_tile per request back to back
+    (each after its own gbd_load_reads), then all at once through a server."""
+    import torch
+    from paper_1803_02272_gb300 import synth
+    reqs = synth.workload_served_queries(n_requests, 1.0, seed=seed, nq_hi=nq_hi)
+    total_pairs = sum(r.reads.n for r in reqs) * ref_rs.n
+    out = torch.empty((max(r.reads.n for r in reqs), ref_rs.n), dtype=torch.int16, device=dev)
+    q0 = ctx.load(reqs[0].reads)
+    ctx.tile(q0, 0, q0.n, ref, 0, ref.n, out=out.view(-1))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in reqs:
+        qh = ctx.load(r.reads)
+        ctx.tile(qh, 0, qh.n, ref, 0, ref.n, out=out.view(-1))
+    torch.cuda.synchronize()
+    plain_pps = total_pairs / (time.perf_counter() - t0)
+    del out
+    burst = serve_phase(gbd, ctx, ref, ref_rs, dev, n_requests, seed=seed, check=True, burst=True, nq_hi=nq_hi)
+    return {"requests": len(reqs), "queries_per_request": f"log-U[1,{nq_hi}]",
+            "plain_sequential_pairs_per_s": plain_pps, "server_burst": burst,
+            "server_vs_plain": burst["pairs_per_s"] / plain_pps}
 
 
 def run_serve_mode(args):
@@ -659,46 +811,19 @@ def run_serve_mode(args):
     ref_rs = synth.workload_paper_scale(n=args.n)
     ctx = gbd.Context(0)
     ref = ctx.load(ref_rs)
-    reqs = synth.workload_served_queries(args.serve_requests, 1.0, seed=1006)
-    total_pairs = sum(r.reads.n for r in reqs) * ref_rs.n
-    # plain: one gbd_tile per request, back to back
-    out = torch.empty((4096, ref_rs.n), dtype=torch.int16, device=dev)
-    q0 = ctx.load(reqs[0].reads)
-    ctx.tile(q0, 0, q0.n, ref, 0, ref.n, out=out.view(-1))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for r in reqs:
-        qh = ctx.load(r.reads)
-        ctx.tile(qh, 0, qh.n, ref, 0, ref.n, out=out.view(-1))
-    torch.cuda.synchronize()
-    plain_pps = total_pairs / (time.perf_counter() - t0)
-    burst = serve_phase(gbd, ctx, ref, ref_rs, dev, args.serve_requests, seed=1006,
-                        check=True, burst=True)
+    cmp_big = serve_compare(gbd, ctx, ref, ref_rs, dev, args.compare_requests, seed=1006)
+    burst = cmp_big["server_burst"]
     loads = {}
     for load in (0.5, 0.8, 0.95):
         loads[str(load)] = serve_phase(gbd, ctx, ref, ref_rs, dev, args.serve_requests, load=load,
-                                       capacity_pps=burst["pairs_per_s"], seed=2000 + int(load * 100))
+                                       capacity_pps=burst["pairs_per_s"], seed=1005)
     # many small requests (1-16 reads each): per-request launch and set-up costs dominate a
     # plain loop, and the server folds concurrent requests into shared launches
-    small = synth.workload_served_queries(args.small_requests, 1.0, seed=1007, nq_hi=16)
-    small_pairs = sum(r.reads.n for r in small) * ref_rs.n
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for r in small:
-        qh = ctx.load(r.reads)
-        ctx.tile(qh, 0, qh.n, ref, 0, ref.n, out=out.view(-1))
-    torch.cuda.synchronize()
-    small_plain_pps = small_pairs / (time.perf_counter() - t0)
-    small_burst = serve_phase(gbd, ctx, ref, ref_rs, dev, args.small_requests, seed=1007, check=True,
-                              burst=True, nq_hi=16)
-    line = {"mode": "serve", "reference_reads": ref_rs.n, "requests": len(reqs),
-            "plain_sequential_pairs_per_s": plain_pps, "server_burst": burst,
-            "server_under_load": loads,
-            "server_vs_plain": burst["pairs_per_s"] / plain_pps,
-            "small_requests": {"requests": len(small), "queries_per_request": "log-U[1,16]",
-                               "plain_sequential_pairs_per_s": small_plain_pps,
-                               "server_burst": small_burst,
-                               "server_vs_plain": small_burst["pairs_per_s"] / small_plain_pps}}
+    cmp_small = serve_compare(gbd, ctx, ref, ref_rs, dev, args.small_requests, seed=1007, nq_hi=16)
+    line = {"mode": "serve", "reference_reads": ref_rs.n, "requests": args.serve_requests,
+            "plain_sequential_pairs_per_s": cmp_big["plain_sequential_pairs_per_s"], "server_burst": burst,
+            "server_under_load": loads, "server_vs_plain": cmp_big["server_vs_plain"],
+            "small_requests": cmp_small}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -99,6 +99,21 @@ def test_cpu_baseline_leg_checks_what_it_is_given():
     got[3] += 1
     assert bench.cpu_baseline_pairs(rs, i, j, got=got)["check"]["mismatches"] == 1
 
+    # the batched workload's check: all pairs of small samples, sampled pairs of the others
+    samples = [rs.subset(range(0, 30)), rs.subset(range(30, 150))]
+
+    def got_ok(s, i, j):
+        return oracle.pairs(samples[s], i, j)
+
+    def got_bad(s, i, j):
+        d = oracle.pairs(samples[s], i, j).copy()
+        d[-1] ^= 1
+        return d
+
+    b = bench.cpu_baseline_batch(samples, got_ok, all_pairs_upto=40, per_sample=100)
+    assert b["kind"] == "oracle" and b["check"] == {"pairs_checked": 435 + 100, "mismatches": 0}
+    assert bench.cpu_baseline_batch(samples, got_bad, all_pairs_upto=40, per_sample=100)["check"]["mismatches"] == 2
+
     th = type("T", (), {"num": 6, "den": 100, "abs_max": 65535})()
     tri = oracle.all_pairs(rs)
     labels = oth.components(n, oth.threshold_edges(tri, rs.lengths, 6, 100))
