@@ -1025,7 +1025,7 @@ def run_components_mode(args):
                        "l2": "10 GB triangle, larger than L2; 512 MiB flush between steps"},
             "roofline": {"bound": "hbm", "achieved": bytes_alg / t / 1e9, "peak": hbm, "unit": "GB/s",
                          "frac": bytes_alg / t / 1e9 / hbm, "traffic": None,
-                         "kernel": "tri_union_kernel + iota/flatten (one gbd_tri_components call)",
+                         "kernel": "span_epilogue_kernel, triangle layout, with hit_bound, hook, union and flatten (one gbd_tri_components call)",
                          "peak_source": "of measured: MEASURED_PEAKS hbm_gbs (copy)"},
             "components": int(len(np.unique(lab))), "edges": ne, "clocks": clocks,
             "gpu_launches": int(launches), "spot_check": check, "cpu_baseline": base,
@@ -1172,7 +1172,7 @@ def run_annotate_mode(args):
                                    "ancestor (200 species)", "pairs": nq * nr},
             "roofline": {"bound": "hbm", "achieved": bytes_alg / t_ep / 1e9, "peak": hbm, "unit": "GB/s",
                          "frac": bytes_alg / t_ep / 1e9 / hbm, "traffic": None,
-                         "kernel": "rect_epilogue_kernel (one gbd_rect_hits call)",
+                         "kernel": "span_epilogue_kernel, rectangle layout (one gbd_rect_hits call)",
                          "peak_source": "of measured: MEASURED_PEAKS hbm_gbs (copy)"},
             "epilogue_ms": t_ep * 1e3, "hits": n_hits,
             "assigned": int((lab >= 0).sum()), "ambiguous": int((lab == -2).sum()), "unassigned": int((lab == -1).sum()),
