@@ -301,6 +301,21 @@ const char *gbd_last_error(void);
  * launched in the process so far (all contexts, all devices). */
 uint64_t gbd_kernel_launches(void);
 
+/* Bounds-checked debug build (no paper counterpart).  A library compiled with
+ * -DGBD_BOUNDS_CHECK=1 (paper_1803_02272_gb300.build.build(check=True) makes
+ * libgbd_check.so beside libgbd.so) checks every distance store, every index into the
+ * general kernel's boundary rows and every shared-memory access window of the systolic
+ * kernel against the extent of its buffer; an access out of range is skipped, so nothing
+ * faults (the results are then wrong, and the violation says where).
+ * gbd_bounds_check waits for the device, writes the smallest out-of-range index recorded
+ * since its last call, tagged with its site in the top 8 bits (1 systolic store, 2 systolic
+ * shared memory, 3 general store, 4 general boundary rows), or UINT64_MAX when there was
+ * none, and clears it.  gbd_debug_output_limit caps the output extent that the context's
+ * next calls check against (0: the real extent), so a test can make stores run past it.
+ * In a build without checks both return ENOTFOUND (*violation = UINT64_MAX). */
+int gbd_bounds_check(uint64_t *violation);
+int gbd_debug_output_limit(gbd_ctx *ctx, uint64_t limit);
+
 /* Measurement support (no paper counterpart): issue rate of one instruction form of the
  * DP inner loop,
  * in lane operations per second (op codes GBD_PROBE_*), timed with CUDA events

@@ -18,6 +18,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgbd.so")
+# the bounds-checked debug build (every distance store and shared-memory window checked)
+CHECK_OBJ = os.path.join(PKG, "_build", "check")
+CHECK_LIB = os.path.join(PKG, "libgbd_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -46,16 +49,21 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=(), check: bool = False) -> str:
+    """Builds libgbd.so, or with check=True the bounds-checked debug library libgbd_check.so
+    (-DGBD_BOUNDS_CHECK=1, objects kept apart); returns the library's path."""
     nvcc = _nvcc()
-    os.makedirs(OBJ, exist_ok=True)
+    obj_dir, lib = (CHECK_OBJ, CHECK_LIB) if check else (OBJ, LIB)
+    if check:
+        extra_flags = list(extra_flags) + ["-DGBD_BOUNDS_CHECK=1"]
+    os.makedirs(obj_dir, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + \
         [os.path.join(os.path.dirname(PKG), "include", "gbd.h")]
     objs = []
     jobs = []
     for src in sources:
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             cmd = [nvcc] + ARCH + NVCC_FLAGS + list(extra_flags) + ["-c", src, "-o", obj]
@@ -68,18 +76,18 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
                 sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed on {cmd[-3]}")
-    if force or jobs or _stale(LIB, objs):
+    if force or jobs or _stale(lib, objs):
         libdir = _cuda_lib_dir(nvcc)
-        tmp = LIB + f".tmp{os.getpid()}"
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + \
             ["-Xlinker", "-rpath," + libdir, "-L" + libdir]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
-            raise RuntimeError("linking libgbd.so failed")
-        os.replace(tmp, LIB)
-    return LIB
+            raise RuntimeError(f"linking {os.path.basename(lib)} failed")
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, check="--check" in sys.argv))

@@ -108,6 +108,7 @@ static int long_rows_general(gbd_ctx *ctx, const gbd_set *set, uint16_t *d_tri, 
     gj.nrows = sc.nlong;
     gj.row_prefix = sc.d_long_prefix;
     gj.units_total = sc.long_units;
+    gj.out_len = out_extent(ctx, set->n * (set->n - 1) / 2);
     return run_general(gj, scoring_of(ctx), ctx->sm_count, st);
 }
 
@@ -137,6 +138,7 @@ static int all_pairs_systolic(gbd_ctx *ctx, gbd_set *set, uint16_t *d_tri, cudaS
     job.mode = OUT_TRI;
     job.conversion = ctx->params.conversion;
     job.gap_open = ctx->params.gap_open;
+    job.out_len = out_extent(ctx, set->n * (set->n - 1) / 2);
     SysJob *d_job = nullptr;
     if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
     rc = run_systolic(d_job, sc.plan, ctx->sm_count, st, &ctx->streams, kDefaultAuxStreams, job.gap_open > 0);
@@ -151,6 +153,7 @@ static int all_pairs_impl(gbd_ctx *ctx, const gbd_set *set, uint16_t *d_tri, cud
     if (use_systolic(ctx)) return all_pairs_systolic(ctx, const_cast<gbd_set *>(set), d_tri, st);
     const uint64_t n = set->n;
     GeneralJob job{set->view(), set->view(), 0, n, 0, n, 0, OUT_TRI, d_tri};
+    job.out_len = out_extent(ctx, n * (n - 1) / 2);
     return run_general(job, scoring_of(ctx), ctx->sm_count, st);
 }
 
@@ -158,8 +161,10 @@ static int all_pairs_impl(gbd_ctx *ctx, const gbd_set *set, uint16_t *d_tri, cud
 static int tile_impl(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd_set *B,
                      uint64_t b0, uint64_t b1, uint16_t *d_out, uint64_t ld, cudaStream_t st)
 {
+    const uint64_t rect_len = out_extent(ctx, (a1 - a0 - 1) * ld + (b1 - b0));
     if (!use_systolic(ctx)) {
         GeneralJob job{A->view(), B->view(), a0, a1, b0, b1, ld, OUT_RECT, d_out};
+        job.out_len = rect_len;
         return run_general(job, scoring_of(ctx), ctx->sm_count, st);
     }
     std::vector<SysEntry> entries;
@@ -186,6 +191,7 @@ static int tile_impl(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, c
         job.mode = OUT_RECT;
         job.conversion = ctx->params.conversion;
         job.gap_open = ctx->params.gap_open;
+        job.out_len = rect_len;
         SysJob *d_job = nullptr;
         SysPlan plan;
         if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
@@ -202,6 +208,7 @@ static int tile_impl(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, c
         GeneralJob gj{A->view(), B->view(), a0, a1, b0, b1, ld, OUT_RECT, d_out};
         gj.rows = d_rows;
         gj.nrows = long_rows.size();
+        gj.out_len = rect_len;
         rc = run_general(gj, scoring_of(ctx), ctx->sm_count, st);
         cudaFreeAsync(d_rows, st);
     }
@@ -216,8 +223,10 @@ static int band_impl(gbd_ctx *ctx, const gbd_set *set, uint64_t a0, uint64_t a1,
 {
     const uint64_t n = set->n;
     if (a1 <= a0 || a0 + 1 >= n) return GBD_OK;
+    const uint64_t band_len = out_extent(ctx, (a1 - a0) * ld);
     if (!use_systolic(ctx)) {
         GeneralJob job{set->view(), set->view(), a0, a1, a0 + 1, n, ld, OUT_RECT, out};
+        job.out_len = band_len;
         return run_general(job, scoring_of(ctx), ctx->sm_count, st);
     }
     std::vector<SysEntry> entries;
@@ -243,6 +252,7 @@ static int band_impl(gbd_ctx *ctx, const gbd_set *set, uint64_t a0, uint64_t a1,
         job.mode = OUT_RECT;
         job.conversion = ctx->params.conversion;
         job.gap_open = ctx->params.gap_open;
+        job.out_len = band_len;
         SysJob *d_job = nullptr;
         SysPlan plan;
         if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
@@ -261,6 +271,7 @@ static int band_impl(gbd_ctx *ctx, const gbd_set *set, uint64_t a0, uint64_t a1,
         GeneralJob gj{set->view(), set->view(), a0, a1, a0 + 1, n, ld, OUT_RECT, out};
         gj.rows = d_rows;
         gj.nrows = long_rows.size();
+        gj.out_len = band_len;
         rc = run_general(gj, scoring_of(ctx), ctx->sm_count, st);
         cudaFreeAsync(d_rows, st);
     }
@@ -362,6 +373,7 @@ static int capture_batch(gbd_ctx *ctx, BatchGraph *bg, const gbd_set *const *sam
         job.mode = OUT_TRI;
         job.conversion = ctx->params.conversion;
         job.gap_open = ctx->params.gap_open;
+        job.out_len = out_extent(ctx, set->n < 2 ? 0 : set->n * (set->n - 1) / 2);
         for (uint64_t i = 0; i + 1 < set->n; ++i) {
             if (set->h_len[i] > kSystolicMaxQuery) continue;
             entries.push_back({(uint32_t)s, (uint32_t)i, (uint32_t)(i + 1), (uint32_t)(set->n - 1 - i)});
@@ -819,6 +831,7 @@ int gbd_batch(gbd_ctx *ctx, const gbd_set *const *samples, uint64_t ns, uint16_t
             const uint64_t n = samples[s]->n;
             if (n < 2) continue;
             GeneralJob job{samples[s]->view(), samples[s]->view(), 0, n, 0, n, 0, OUT_TRI, d_tris[s]};
+            job.out_len = out_extent(ctx, n * (n - 1) / 2);
             int rc = run_general(job, scoring_of(ctx), ctx->sm_count, st);
             if (rc != GBD_OK) return rc;
         }
@@ -909,6 +922,25 @@ int gbd_batch_tuning(const gbd_ctx *ctx, uint32_t capacity, double *trial_ms, do
 }
 
 uint64_t gbd_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int gbd_bounds_check(uint64_t *violation)
+{
+    if (!violation) return fail(GBD_EINVAL, "gbd_bounds_check: NULL argument");
+    *violation = ~0ull;
+    if (!GBD_BOUNDS_CHECK) return fail(GBD_ENOTFOUND, "gbd_bounds_check: the library was built without bounds checks");
+    GBD_CUDA_TRY(cudaDeviceSynchronize());        // every launch so far has finished
+    *violation = std::min(bounds_take_systolic(), bounds_take_general());
+    return GBD_OK;
+}
+
+int gbd_debug_output_limit(gbd_ctx *ctx, uint64_t limit)
+{
+    if (!ctx) return fail(GBD_EINVAL, "gbd_debug_output_limit: NULL context");
+    if (!GBD_BOUNDS_CHECK)
+        return fail(GBD_ENOTFOUND, "gbd_debug_output_limit: the library was built without bounds checks");
+    ctx->debug_out_limit = limit;
+    return GBD_OK;
+}
 
 int gbd_probe_op_rate(int op, uint32_t iters, double *lane_ops_per_s, void *stream)
 {

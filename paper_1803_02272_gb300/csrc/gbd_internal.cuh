@@ -26,6 +26,40 @@ int cuda_fail(cudaError_t e, const char *what);
 // Count of kernel launches made by the library (see gbd_kernel_launches).
 void note_launches(uint64_t k);
 
+// ------------------------------------------------------------------ bounds-checked build
+// Compiled with -DGBD_BOUNDS_CHECK=1 (a debug build of the library), every distance store,
+// every index into the general kernel's boundary-row scratch and every write into (and the
+// read window of) the systolic kernel's shared-memory profile ring checks its index
+// against the extent of its buffer.  An index out of range is not used (nothing faults;
+// a read window is moved to a harmless in-range place, so results are wrong but no
+// access leaves its buffer) and the smallest such index, tagged with its site in the top
+// 8 bits, is kept in a device word of the kernel's source file; gbd_bounds_check reads
+// and clears it.  Without the flag the checks compile to nothing.
+#ifndef GBD_BOUNDS_CHECK
+#define GBD_BOUNDS_CHECK 0
+#endif
+enum BoundsSite : unsigned {
+    BOUNDS_SYSTOLIC_OUT = 1,      // a systolic distance store
+    BOUNDS_SYSTOLIC_RING = 2,     // the systolic profile ring / table (shared memory)
+    BOUNDS_GENERAL_OUT = 3,       // a general-kernel distance store
+    BOUNDS_GENERAL_SCRATCH = 4,   // the general kernel's boundary rows
+};
+#if GBD_BOUNDS_CHECK
+static __device__ unsigned long long g_bounds_first = ~0ull;
+__device__ __forceinline__ bool bounds_ok(uint64_t idx, uint64_t extent, unsigned site)
+{
+    if (idx < extent) return true;
+    atomicMin(&g_bounds_first, ((unsigned long long)site << 56) | (idx & ((1ull << 56) - 1)));
+    return false;
+}
+#else
+__device__ __forceinline__ bool bounds_ok(uint64_t, uint64_t, unsigned) { return true; }
+#endif
+// Reads and clears the source file's word (UINT64_MAX when nothing was recorded or the
+// build has no checks).
+uint64_t bounds_take_systolic();
+uint64_t bounds_take_general();
+
 // Score-to-distance rule (GBD_CONV_*) applied to the local score S of reads of lengths
 // la and lb; the result is stored as uint16.  GBD_CONV_NORM divides in 32 bits: 65535 * x
 // with x <= m <= 65535 stays below 2^32.
@@ -113,7 +147,15 @@ struct gbd_ctx {
     void *mds_w = nullptr;
     size_t mds_w_bytes = 0;
     cudaEvent_t mds_w_done = nullptr; // recorded after the last work that used mds_w
+    uint64_t debug_out_limit = 0;     // bounds-checked builds: cap on the output extents (0 = none)
 };
+
+// The output extent a job of this context checks against: `real`, or the debug cap of a
+// bounds-checked build when it is smaller.
+inline uint64_t out_extent(const gbd_ctx *ctx, uint64_t real)
+{
+    return (GBD_BOUNDS_CHECK && ctx->debug_out_limit && ctx->debug_out_limit < real) ? ctx->debug_out_limit : real;
+}
 
 struct gbd_set {
     gbd_ctx *ctx = nullptr;
@@ -162,6 +204,7 @@ struct GeneralJob {
     uint64_t nrows = 0;
     const uint64_t *row_prefix = nullptr;   // OUT_TRI_ROWS: pairs before each listed row
     uint64_t units_total = 0;               // OUT_TRI_ROWS: row_prefix[nrows]
+    uint64_t out_len = 0;                   // entries of out (checked in bounds-checked builds)
 };
 int run_general(const GeneralJob &job, const Scoring &sc, int sm_count, cudaStream_t stream);
 // Same kernel on a rectangle job, with boundary rows in caller-provided scratch

@@ -128,6 +128,7 @@ extern "C" int gbd_tile_noalloc(gbd_ctx *ctx, const uint8_t *d_seqA, const uint6
                                         std::to_string(h_flags[2 + s]) + " of " + (s ? "B" : "A") +
                                         " is not one of A, C, G, T");
     GeneralJob job{{wA, lA, nA, stride}, {wB, lB, nB, stride}, 0, nA, 0, nB, ld, OUT_RECT, d_out};
+    job.out_len = out_extent(ctx, (nA - 1) * ld + nB);
     const Scoring sc{ctx->params.match, ctx->params.mismatch, ctx->params.gap, ctx->params.conversion,
                      ctx->params.gap_open};
     return run_general_in(job, sc, bnd, bnd_ints, ctx->sm_count, st);

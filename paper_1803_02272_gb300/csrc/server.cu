@@ -209,6 +209,7 @@ std::string launch_batch(gbd_server *srv, const std::vector<Piece> &pieces, cuda
         J.mode = OUT_RECT;
         J.conversion = ctx->params.conversion;
         J.gap_open = ctx->params.gap_open;
+        J.out_len = out_extent(ctx, r->nq * ref->n);
         const uint32_t job = (uint32_t)jobs.size();
         jobs.push_back(J);
         std::vector<uint32_t> long_rows;
@@ -230,6 +231,7 @@ std::string launch_batch(gbd_server *srv, const std::vector<Piece> &pieces, cuda
             GeneralJob gj{J.Q, J.S, 0, r->nq, 0, ref->n, ref->n, OUT_RECT, r->d_rows};
             gj.rows = d_list;
             gj.nrows = long_rows.size();
+            gj.out_len = J.out_len;
             general.push_back(gj);
         }
     }

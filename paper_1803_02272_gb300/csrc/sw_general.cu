@@ -52,14 +52,21 @@ __device__ __forceinline__ void tri_unindex(uint64_t k, uint64_t n, uint64_t &i,
 // E = max(E_l - gap, H_l - gap_open - gap), F = max(F_u - gap, H_u - gap_open - gap).
 template <bool AFFINE>
 __global__ void __launch_bounds__(128)
-sw_general_kernel(GeneralJob job, Scoring sc, int *__restrict__ scratch, uint64_t units)
+sw_general_kernel(GeneralJob job, Scoring sc, int *__restrict__ scratch, uint64_t units, uint64_t scratch_ints)
 {
+    (void)scratch_ints;                             // checked in bounds-checked builds
     constexpr int NEG = -(1 << 28);
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
     int *bnd = scratch + tid;                       // bnd[j * nthr] = H(strip top - 1, j)
     // affine: F(strip top - 1, j) in the second half of the scratch
-    int *bndf = scratch + (uint64_t)(job.B.stride * kBasesPerWord + 1) * nthr + tid;
+    const uint64_t foff = (uint64_t)(job.B.stride * kBasesPerWord + 1) * nthr;
+    int *bndf = scratch + foff + tid;
+    // the boundary-row entry of column j is in the scratch (always, unless the build
+    // checks bounds and finds it is not)
+    auto in_scratch = [&](uint64_t j, uint64_t off) {
+        return bounds_ok(off + j * nthr + tid, scratch_ints, BOUNDS_GENERAL_SCRATCH);
+    };
     const uint64_t nb = job.b1 - job.b0;
     const int goe = sc.gap_open + sc.gap;
 
@@ -99,9 +106,9 @@ sw_general_kernel(GeneralJob job, Scoring sc, int *__restrict__ scratch, uint64_
             int diag_top = 0;                                // H(i0, 0) = 0
             for (int j = 1; j <= lb; ++j) {
                 const uint32_t c = base_at(b, j - 1);
-                int up = (i0 == 0) ? 0 : bnd[(uint64_t)j * nthr];   // H(i0, j)
-                int fup = NEG;                                        // F(i0, j)
-                if (AFFINE && i0 != 0) fup = bndf[(uint64_t)j * nthr];
+                int up = (i0 == 0 || !in_scratch(j, 0)) ? 0 : bnd[(uint64_t)j * nthr];   // H(i0, j)
+                int fup = NEG;                                                          // F(i0, j)
+                if (AFFINE && i0 != 0 && in_scratch(j, foff)) fup = bndf[(uint64_t)j * nthr];
                 int diag = diag_top;                                  // H(i0, j-1)
                 diag_top = up;
 #pragma unroll
@@ -123,11 +130,11 @@ sw_general_kernel(GeneralJob job, Scoring sc, int *__restrict__ scratch, uint64_
                     up = h;
                     if (i0 + r < la) best = max(best, h);
                 }
-                bnd[(uint64_t)j * nthr] = hl[kStrip - 1];
-                if (AFFINE) bndf[(uint64_t)j * nthr] = fup;
+                if (in_scratch(j, 0)) bnd[(uint64_t)j * nthr] = hl[kStrip - 1];
+                if (AFFINE && in_scratch(j, foff)) bndf[(uint64_t)j * nthr] = fup;
             }
         }
-        job.out[o] = score_to_distance(best, la, lb, sc.conversion);
+        if (bounds_ok(o, job.out_len, BOUNDS_GENERAL_OUT)) job.out[o] = score_to_distance(best, la, lb, sc.conversion);
     }
 }
 
@@ -171,10 +178,11 @@ int run_general(const GeneralJob &job, const Scoring &sc, int sm_count, cudaStre
     if (blocks > need_blocks) blocks = need_blocks;
     int *scratch = nullptr;
     GBD_CUDA_TRY(cudaMallocAsync((void **)&scratch, blocks * threads * per_thread, stream));
+    const uint64_t sints = blocks * threads * per_thread / sizeof(int);
     if (sc.gap_open > 0)
-        sw_general_kernel<true><<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units);
+        sw_general_kernel<true><<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units, sints);
     else
-        sw_general_kernel<false><<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units);
+        sw_general_kernel<false><<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units, sints);
     note_launches(1);
     cudaError_t le = cudaGetLastError();
     cudaError_t fe = cudaFreeAsync(scratch, stream);
@@ -198,13 +206,25 @@ int run_general_in(const GeneralJob &job, const Scoring &sc, int *scratch, uint6
     const uint64_t need_blocks = (units + threads - 1) / threads;
     if (blocks > need_blocks) blocks = need_blocks;
     if (sc.gap_open > 0)
-        sw_general_kernel<true><<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units);
+        sw_general_kernel<true><<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units, scratch_ints);
     else
-        sw_general_kernel<false><<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units);
+        sw_general_kernel<false><<<(unsigned)blocks, threads, 0, stream>>>(job, sc, scratch, units, scratch_ints);
     note_launches(1);
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) return cuda_fail(le, "sw_general_kernel launch");
     return GBD_OK;
+}
+
+uint64_t bounds_take_general()
+{
+#if GBD_BOUNDS_CHECK
+    unsigned long long v = ~0ull, reset = ~0ull;
+    if (cudaMemcpyFromSymbol(&v, g_bounds_first, sizeof v) != cudaSuccess) v = ~0ull;
+    cudaMemcpyToSymbol(g_bounds_first, &reset, sizeof reset);
+    return v;
+#else
+    return ~0ull;
+#endif
 }
 
 }  // namespace gbd

@@ -168,7 +168,8 @@ __device__ __forceinline__ void describe_chunks(const SysJob &J, const SysUnit &
         e.y = ((alo & 2u) ? 0x0000ffffu : 0u) | ((ahi & 2u) ? 0xffff0000u : 0u);
         e.z = (blo & 0xffffu) | (bhi << 16);
         e.w = (blo >> 16) | (bhi & 0xffff0000u);
-        *reinterpret_cast<uint4 *>(table + 4 * (tslot + (int)t)) = e;
+        if (bounds_ok((uint64_t)(tslot + (int)t), RING_CHUNKS, BOUNDS_SYSTOLIC_RING))
+            *reinterpret_cast<uint4 *>(table + 4 * (tslot + (int)t)) = e;
     }
     // state at chunk b16 + 16, from the half's lane 15
     const uint32_t nxt = last ? (p + 1u) : (p | (valid ? (ckt + 1u) << 16 : 0u));
@@ -201,9 +202,9 @@ __device__ __forceinline__ void fill_chunk(uint32_t *ws, int lane, int m, uint32
         const uint32_t ne = __vminu2(codes ^ (q * ONE2), ONE2);   // 0 where the base matches, else 1
         const uint32_t v = lop_sel(0x00030003u - ne - ne, NEG2, pad);
         uint32_t *arr = ws + q * PWORDS;
-        arr[pslot(rho)] = v;
-        if (rho < 32) arr[pslot(rho + RING)] = v;
-        if (rho >= RING - 16) arr[pslot(rho - RING)] = v;
+        if (bounds_ok(pslot(rho), PWORDS, BOUNDS_SYSTOLIC_RING)) arr[pslot(rho)] = v;
+        if (rho < 32 && bounds_ok(pslot(rho + RING), PWORDS, BOUNDS_SYSTOLIC_RING)) arr[pslot(rho + RING)] = v;
+        if (rho >= RING - 16 && bounds_ok(pslot(rho - RING), PWORDS, BOUNDS_SYSTOLIC_RING)) arr[pslot(rho - RING)] = v;
     }
 }
 
@@ -214,8 +215,9 @@ __device__ __forceinline__ uint2 lds64(const uint32_t *ws_words, uint32_t byte_o
 
 template <int R, bool AFFINE>
 __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint32_t *ws, int lane,
-                                      int neg_rel, uint32_t *err)
+                                      int neg_rel, int ws_words, uint32_t *err)
 {
+    (void)ws_words;                           // the warp region's offset (bounds-checked builds)
     constexpr int D = CH - R;                 // delay steps between lanes
     const int la = J.Q.len[u.q];
     const uint32_t *qwords = J.Q.words + (uint64_t)u.q * J.Q.stride;
@@ -314,6 +316,15 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
         }
 
         const int m_c1 = (m_c == RING_CHUNKS - 1) ? 0 : m_c + 1;   // table slot of the second chunk
+#if GBD_BOUNDS_CHECK
+        // the words a row reads in these two chunks: from 18 before its chunk base to 38
+        // after it (the second chunk's last 64-bit load); a window leaving the block's shared
+        // memory is moved onto the block's padding profile
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (!bounds_ok((uint64_t)(ws_words + (int)(addr[r] / 4u) + 38), BLOCK_WORDS, BOUNDS_SYSTOLIC_RING))
+                addr[r] = (uint32_t)((neg_rel + 18) * 4);
+#endif
 #pragma unroll
         for (int h2 = 0; h2 < 2; ++h2) {
             const int g = g0 + h2;
@@ -448,6 +459,7 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
                             } else {
                                 idx = ((uint64_t)u.q - J.row0) * J.ld + ((uint64_t)so - J.col0);
                             }
+                            if (bounds_ok(idx, J.out_len, BOUNDS_SYSTOLIC_OUT))
                             J.out[idx] = score_to_distance(S, la, lb, conv);
                         }
                     }
@@ -500,7 +512,7 @@ sw_systolic_kernel(const SysJob *__restrict__ jobs, const SysEntry *__restrict__
         u.q = en.q;
         u.sub_begin = en.sub_begin + piece * piece_len;
         u.nsub = min(piece_len, en.nsub - piece * piece_len);
-        run_unit<R, AFFINE>(jobs[u.job], u, ws, lane, neg_rel, err);
+        run_unit<R, AFFINE>(jobs[u.job], u, ws, lane, neg_rel, warp * WARP_WORDS, err);
         __syncwarp();
     }
 }
@@ -697,6 +709,18 @@ int run_systolic(const SysJob *d_jobs, const SysPlan &plan, int sm_count, cudaSt
 }  // namespace gbd
 
 namespace gbd {
+uint64_t bounds_take_systolic()
+{
+#if GBD_BOUNDS_CHECK
+    unsigned long long v = ~0ull, reset = ~0ull;
+    if (cudaMemcpyFromSymbol(&v, g_bounds_first, sizeof v) != cudaSuccess) v = ~0ull;
+    cudaMemcpyToSymbol(g_bounds_first, &reset, sizeof reset);
+    return v;
+#else
+    return ~0ull;
+#endif
+}
+
 int systolic_resident_warps(int sm_count)
 {
     // shared memory bound: BLOCKS_PER_SM blocks of WARPS_PER_BLOCK warps per SM

@@ -20,6 +20,7 @@ struct SysJob {
     int mode;                   // OUT_TRI or OUT_RECT
     int conversion;
     int gap_open;               // affine gaps (extend 1) when > 0; launch with affine = true
+    uint64_t out_len;           // entries of out (checked in bounds-checked builds)
 };
 
 // One query (original index q in Q, length <= 512) against the subjects at list

@@ -34,7 +34,7 @@ EXPORTS = [
     "gbd_server_wait", "gbd_server_destroy", "gbd_last_error", "gbd_probe_op_rate",
     "gbd_kernel_launches", "gbd_tile_noalloc", "gbd_sqdist_square", "gbd_gram_apply", "gbd_mds",
     "gbd_tile_hits", "gbd_threshold_components", "gbd_tri_components", "gbd_batch_tuning",
-    "gbd_rect_hits",
+    "gbd_rect_hits", "gbd_bounds_check", "gbd_debug_output_limit",
 ]
 
 
@@ -92,6 +92,8 @@ def _declare(lib):
         "gbd_rect_hits": ([vp, vp, u64, u64, vp, u64, u64, vp, u64, ctypes.POINTER(GbdThreshold), vp, u64,
                            vp, vp, vp, vp], ci),
         "gbd_tri_components": ([vp, vp, vp, ctypes.POINTER(GbdThreshold), vp, vp, vp], ci),
+        "gbd_bounds_check": ([ctypes.POINTER(u64)], ci),
+        "gbd_debug_output_limit": ([vp, u64], ci),
         "gbd_batch_tuning": ([vp, u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_int32),
                               ctypes.POINTER(ci)], ci),

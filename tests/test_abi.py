@@ -70,3 +70,13 @@ def test_probe_op_names_match_header():
     count = codes.pop("COUNT")
     assert sorted(codes.values()) == list(range(count))
     assert [name for name, _ in sorted(codes.items(), key=lambda kv: kv[1])] == gbd.PROBE_OPS
+
+
+def test_default_build_has_no_bounds_checks():
+    """The debug entry points exist in the default library and report that its kernels
+    carry no checks (the checked library is a separate build)."""
+    from paper_1803_02272_gb300 import gbd
+    v = ctypes.c_uint64(0)
+    assert gbd._lib.gbd_bounds_check(ctypes.byref(v)) == gbd.GBD_ENOTFOUND
+    assert v.value == (1 << 64) - 1
+    assert gbd._lib.gbd_debug_output_limit(None, 5) == gbd.GBD_EINVAL
