@@ -74,7 +74,7 @@ def parse_args(argv=None):
                     help="offered load of that phase, as a fraction of measured pairs/s")
     ap.add_argument("--samples", type=int, default=64, help="batch mode: samples")
     ap.add_argument("--small-requests", type=int, default=400,
-                    help="serve mode: requests of the small-request comparison")
+                    help="requests of 1-16 reads in the small-request served-vs-plain comparison (0 = skip)")
     ap.add_argument("--mds-k", type=int, default=64, help="mds mode: sketch columns k")
     ap.add_argument("--mds-r", type=int, default=50, help="mds mode: coordinates r (paper: 50)")
     ap.add_argument("--mds-q", type=int, default=2, help="mds mode: subspace-iteration rounds")
@@ -592,7 +592,7 @@ def optional_phases(args, gbd, ctx, rs, dev, pairs_per_s: float, gcups: float) -
         else:
             out["batch"] = {"skipped": f"time budget: needs about {est:.0f} s, {left():.0f} s left"}
         del samples
-    ref = ctx.load(rs) if (args.compare_requests > 0 or args.serve_requests > 0) else None
+    ref = ctx.load(rs) if (args.compare_requests > 0 or args.small_requests > 0 or args.serve_requests > 0) else None
     capacity = pairs_per_s
     if args.compare_requests > 0:
         reqs = synth.workload_served_queries(args.compare_requests, 1.0, seed=1006)
@@ -602,6 +602,16 @@ def optional_phases(args, gbd, ctx, rs, dev, pairs_per_s: float, gcups: float) -
             capacity = out["serve_vs_plain"]["server_burst"]["pairs_per_s"]
         else:
             out["serve_vs_plain"] = {"skipped": f"time budget: needs about {est:.0f} s, {left():.0f} s left"}
+    if args.small_requests > 0:
+        # many small requests (1-16 reads each): a plain loop pays its per-request launch and
+        # set-up costs, the server folds concurrent requests into shared launches
+        reqs = synth.workload_served_queries(args.small_requests, 1.0, seed=1007, nq_hi=16)
+        est = 0.01 * len(reqs) + 2 * sum(r.reads.n for r in reqs) * rs.n / (0.8 * pairs_per_s) + 15
+        if est < left():
+            out["serve_vs_plain_small"] = serve_compare(gbd, ctx, ref, rs, dev, args.small_requests, seed=1007,
+                                                        nq_hi=16)
+        else:
+            out["serve_vs_plain_small"] = {"skipped": f"time budget: needs about {est:.0f} s, {left():.0f} s left"}
     if args.serve_requests > 0:
         n_req, est = args.serve_requests, None
         while True:

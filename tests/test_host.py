@@ -59,7 +59,8 @@ def test_bench_triangle_write_and_traffic_figures():
     per_pair = bench.traffic_value("dram_bytes_per_pair")
     if per_pair is not None:          # the kernel sources still match the profiled ones
         assert per_pair >= 2.0 and bench.traffic_per_launch(10) == per_pair * 10
-        assert tw["dram_bytes_per_pair"] >= 2.0
+        # the written bytes per pair: the 2 B output, less what a capture leaves in L2
+        assert 1.5 <= tw["dram_bytes_per_pair"] <= per_pair
 
 
 def _bench():
