@@ -293,12 +293,16 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
     int m_fill = 1;
     int m_c = (RING_CHUNKS - lane % RING_CHUNKS) % RING_CHUNKS;
 
-    // Two chunks per iteration: the second one's profile columns lie 18 words (72 bytes)
-    // after the first one's, so it reads them at immediate offsets, and the loop test,
-    // the rebase check and the per-row address advance run once per 32 steps.  Reading
-    // one chunk past the ring's last slot lands in the copy of slot 0 that every fill of
-    // slot 0 also writes.  An extra padding chunk at the end (C + LANES odd) emits nothing.
-    for (int g0 = 0; C < 0 || g0 < C + LANES; g0 += 2) {
+    // Linear gaps: two chunks per iteration.  The second one's profile columns lie 18
+    // words (72 bytes) after the first one's, so it reads them at immediate offsets, and
+    // the loop test, the rebase check and the per-row address advance run once per 32
+    // steps.  Reading one chunk past the ring's last slot lands in the copy of slot 0 that
+    // every fill of slot 0 also writes.  An extra padding chunk at the end (C + LANES odd)
+    // emits nothing.  Affine gaps keep one chunk per iteration: their loop body is twice
+    // as long, and doubling it again cost more (registers, instruction fetch) than the
+    // loop overhead it saves.
+    constexpr int PAIR = AFFINE ? 1 : 2;
+    for (int g0 = 0; C < 0 || g0 < C + LANES; g0 += PAIR) {
         // ---- rebase every REBASE_CHUNKS chunks (all lanes at the same global step)
         if (g0 > 0 && (g0 & (REBASE_CHUNKS - 1)) == 0) {
 #pragma unroll
@@ -326,11 +330,11 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
                 addr[r] = (uint32_t)((neg_rel + 18) * 4);
 #endif
 #pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
+        for (int h2 = 0; h2 < PAIR; ++h2) {
             const int g = g0 + h2;
             // ---- refill: chunk g+1 into the ring (describing the next 16 chunks first when
             // g+1 starts them; g+1 is odd for the first chunk of the pair)
-            if (h2 == 1 && ((g + 1) & 15) == 0) {
+            if ((PAIR == 1 || h2 == 1) && ((g + 1) & 15) == 0) {
                 tslot = (tslot == RING_CHUNKS - 16) ? 0 : tslot + 16;
                 describe_chunks(J, u, lane, hc, (uint32_t)(g + 1), tslot, table, dword, dnv, C);
             }
@@ -469,13 +473,13 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
                 pos_prev = pos_c;
             }
         }
-        // ---- advance the profile addresses by two chunks
+        // ---- advance the profile addresses by the chunks of this iteration
         {
-            const bool wrap = (m_c >= RING_CHUNKS - 2);
-            const uint32_t d = wrap ? (uint32_t)(4 * 18 * (2 - RING_CHUNKS)) : (uint32_t)(4 * 18 * 2);
+            const bool wrap = (m_c >= RING_CHUNKS - PAIR);
+            const uint32_t d = wrap ? (uint32_t)(4 * 18 * (PAIR - RING_CHUNKS)) : (uint32_t)(4 * 18 * PAIR);
 #pragma unroll
             for (int r = 0; r < R; ++r) addr[r] += d;
-            m_c = wrap ? m_c + 2 - RING_CHUNKS : m_c + 2;
+            m_c = wrap ? m_c + PAIR - RING_CHUNKS : m_c + PAIR;
         }
         (void)err;
     }
