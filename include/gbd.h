@@ -127,6 +127,18 @@ double gbd_set_pair_cells(const gbd_set *set);
 int gbd_all_pairs(gbd_ctx *ctx, const gbd_set *set, uint16_t *d_tri, uint64_t tri_len,
                   void *stream);
 
+/* All pairwise distances into host memory (section 2.2's matrix D of a sample, wanted on
+ * the host, or larger than the device memory left for it): the triangle, in the layout of
+ * gbd_all_pairs, is computed in bands of consecutive rows (each band a contiguous run of the
+ * triangle) into two device staging buffers of at most band_entries entries each (0 = 2^28,
+ * two 512 MB buffers; never less than one row, n - 1 entries), and each band is copied to
+ * h_tri while the next one is computed.  h_tri is a HOST pointer to tri_len uint16 entries
+ * (page-locked memory lets the copies overlap the computation; pageable memory works, with
+ * each copy synchronous).  The call synchronises `stream` and returns when the whole
+ * triangle is in h_tri.  EINVAL on a wrong tri_len or a NULL h_tri. */
+int gbd_all_pairs_to_host(gbd_ctx *ctx, const gbd_set *set, uint16_t *h_tri, uint64_t tri_len,
+                          uint64_t band_entries, void *stream);
+
 /* Rectangle (section 2.2: `disseq` on two read files of m and n reads returns the m x n
  * matrix D with d_ij the distance between read i of the first and read j of the second):
  * d_out[(r-a0)*ld + (c-b0)] = d(A[r], B[c])

@@ -278,6 +278,79 @@ static int band_impl(gbd_ctx *ctx, const gbd_set *set, uint64_t a0, uint64_t a1,
     return rc;
 }
 
+// Listed triangle rows of a set through the general kernel, into `out`, which holds the
+// triangle's entries from index `base` on (len entries).
+static int tri_rows_general(gbd_ctx *ctx, const gbd_set *set, const std::vector<uint32_t> &rows_h,
+                            uint16_t *out, uint64_t base, uint64_t len, cudaStream_t st)
+{
+    const uint64_t n = set->n;
+    std::vector<uint64_t> prefix(1, 0);
+    for (uint32_t r : rows_h) prefix.push_back(prefix.back() + (n - 1 - r));
+    if (prefix.back() == 0) return GBD_OK;
+    uint32_t *d_rows = nullptr;
+    uint64_t *d_prefix = nullptr;
+    int rc = upload(rows_h.data(), rows_h.size(), &d_rows, st);
+    if (rc == GBD_OK) rc = upload(prefix.data(), prefix.size(), &d_prefix, st);
+    if (rc == GBD_OK) {
+        GeneralJob gj{set->view(), set->view(), 0, n, 0, n, 0, OUT_TRI_ROWS, out};
+        gj.rows = d_rows;
+        gj.nrows = rows_h.size();
+        gj.row_prefix = d_prefix;
+        gj.units_total = prefix.back();
+        gj.out_base = base;
+        gj.out_len = len;
+        rc = run_general(gj, scoring_of(ctx), ctx->sm_count, st);
+    }
+    if (d_rows) cudaFreeAsync(d_rows, st);
+    if (d_prefix) cudaFreeAsync(d_prefix, st);
+    return rc;
+}
+
+// Rows [a0, a1) of a set's triangle into `out`: the band is the contiguous run of the
+// row-major triangle from k(a0, a0 + 1) on, and `out` holds just that run.
+static int tri_band_impl(gbd_ctx *ctx, const gbd_set *set, uint64_t a0, uint64_t a1, uint16_t *out, cudaStream_t st)
+{
+    const uint64_t n = set->n;
+    const uint64_t base = a0 * n - a0 * (a0 + 1) / 2;
+    const uint64_t len = out_extent(ctx, a1 * n - a1 * (a1 + 1) / 2 - base);
+    std::vector<SysEntry> entries;
+    std::vector<uint8_t> rows;
+    std::vector<uint32_t> general_rows;
+    const bool systolic = use_systolic(ctx);
+    for (uint64_t r = a0; r < a1 && r + 1 < n; ++r) {
+        if (systolic && set->h_len[r] <= kSystolicMaxQuery) {
+            entries.push_back({0u, (uint32_t)r, (uint32_t)(r + 1), (uint32_t)(n - 1 - r)});
+            rows.push_back((uint8_t)systolic_rows(set->h_len[r]));
+        } else {
+            general_rows.push_back((uint32_t)r);
+        }
+    }
+    int rc = GBD_OK;
+    if (!entries.empty()) {
+        SysJob job{};
+        job.Q = job.S = set->view();
+        job.sub_perm = nullptr;
+        job.out = out;
+        job.n = n;
+        job.mode = OUT_TRI;
+        job.conversion = ctx->params.conversion;
+        job.gap_open = ctx->params.gap_open;
+        job.out_len = len;
+        job.out_base = base;
+        SysJob *d_job = nullptr;
+        SysPlan plan;
+        if ((rc = upload(&job, 1, &d_job, st)) != GBD_OK) return rc;
+        rc = build_plan(entries, rows, plan, false, st, 0, set->mean_len, ctx->sm_count);
+        if (rc == GBD_OK)
+            rc = run_systolic(d_job, plan, ctx->sm_count, st, &ctx->streams, kDefaultAuxStreams, job.gap_open > 0);
+        cudaFreeAsync(d_job, st);
+        free_plan(plan, st);
+        if (rc != GBD_OK) return rc;
+    }
+    if (!general_rows.empty()) rc = tri_rows_general(ctx, set, general_rows, out, base, len, st);
+    return rc;
+}
+
 // Default entries of the band scratch of gbd_threshold_components without a triangle (512 MB).
 constexpr uint64_t kBandEntries = 1ull << 28;
 
@@ -670,6 +743,66 @@ int gbd_all_pairs(gbd_ctx *ctx, const gbd_set *set, uint16_t *d_tri, uint64_t tr
     if (!d_tri) return fail(GBD_EINVAL, "gbd_all_pairs: d_tri is NULL");
     GBD_CUDA_TRY(cudaSetDevice(ctx->device));
     return all_pairs_impl(ctx, set, d_tri, (cudaStream_t)stream);
+}
+
+int gbd_all_pairs_to_host(gbd_ctx *ctx, const gbd_set *set, uint16_t *h_tri, uint64_t tri_len,
+                          uint64_t band_entries, void *stream)
+{
+    if (!ctx || !set) return fail(GBD_EINVAL, "gbd_all_pairs_to_host: NULL context or set");
+    const uint64_t n = set->n;
+    const uint64_t need = n < 2 ? 0 : n * (n - 1) / 2;
+    if (tri_len != need)
+        return fail(GBD_EINVAL, "gbd_all_pairs_to_host: tri_len is " + std::to_string(tri_len) +
+                                    ", expected n(n-1)/2 = " + std::to_string(need));
+    if (need == 0) return GBD_OK;
+    if (!h_tri) return fail(GBD_EINVAL, "gbd_all_pairs_to_host: h_tri is NULL");
+    GBD_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStream_t cp = ctx->streams.aux[1];          // copies; the bands' launches use aux[0]
+    // each band: whole rows, at most `cap` entries (at least one row)
+    uint64_t cap = band_entries ? band_entries : kBandEntries;
+    cap = std::min<uint64_t>(std::max<uint64_t>(cap, n - 1), need);
+    uint16_t *buf[2] = {nullptr, nullptr};
+    cudaEvent_t computed[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    int rc = GBD_OK;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMallocAsync((void **)&buf[k], cap * sizeof(uint16_t), st);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&computed[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) rc = cuda_fail(e, "gbd_all_pairs_to_host: staging set-up");
+    uint64_t band = 0;
+    for (uint64_t a0 = 0; rc == GBD_OK && a0 + 1 < n; ++band) {
+        uint64_t a1 = a0, len = 0;
+        while (a1 + 1 < n && len + (n - 1 - a1) <= cap) len += n - 1 - a1++;
+        const int k = (int)(band & 1);
+        // the buffer's previous band must have reached the host before it is overwritten
+        if (band >= 2 && (e = cudaStreamWaitEvent(st, copied[k], 0)) != cudaSuccess) {
+            rc = cuda_fail(e, "cudaStreamWaitEvent");
+            break;
+        }
+        rc = tri_band_impl(ctx, set, a0, a1, buf[k], st);
+        if (rc != GBD_OK) break;
+        const uint64_t base = a0 * n - a0 * (a0 + 1) / 2;
+        if ((e = cudaEventRecord(computed[k], st)) == cudaSuccess && (e = cudaStreamWaitEvent(cp, computed[k], 0)) == cudaSuccess &&
+            (e = cudaMemcpyAsync(h_tri + base, buf[k], len * sizeof(uint16_t), cudaMemcpyDeviceToHost, cp)) == cudaSuccess)
+            e = cudaEventRecord(copied[k], cp);
+        if (e != cudaSuccess) rc = cuda_fail(e, "gbd_all_pairs_to_host: band copy");
+        a0 = a1;
+    }
+    // the triangle is in host memory when the call returns
+    cudaError_t se = cudaStreamSynchronize(cp);
+    cudaError_t se2 = cudaStreamSynchronize(st);
+    for (int k = 0; k < 2; ++k) {
+        if (buf[k]) cudaFreeAsync(buf[k], st);
+        if (computed[k]) cudaEventDestroy(computed[k]);
+        if (copied[k]) cudaEventDestroy(copied[k]);
+    }
+    if (rc != GBD_OK) return rc;
+    if (se != cudaSuccess) return cuda_fail(se, "gbd_all_pairs_to_host: copies");
+    if (se2 != cudaSuccess) return cuda_fail(se2, "gbd_all_pairs_to_host: bands");
+    return GBD_OK;
 }
 
 int gbd_tile(gbd_ctx *ctx, const gbd_set *A, uint64_t a0, uint64_t a1, const gbd_set *B,

@@ -205,6 +205,7 @@ struct GeneralJob {
     const uint64_t *row_prefix = nullptr;   // OUT_TRI_ROWS: pairs before each listed row
     uint64_t units_total = 0;               // OUT_TRI_ROWS: row_prefix[nrows]
     uint64_t out_len = 0;                   // entries of out (checked in bounds-checked builds)
+    uint64_t out_base = 0;                  // OUT_TRI_ROWS: out[k(i,j) - out_base] (a band of rows)
 };
 int run_general(const GeneralJob &job, const Scoring &sc, int sm_count, cudaStream_t stream);
 // Same kernel on a rectangle job, with boundary rows in caller-provided scratch

@@ -84,7 +84,7 @@ sw_general_kernel(GeneralJob job, Scoring sc, int *__restrict__ scratch, uint64_
             }
             ia = job.rows[lo];
             jb = ia + 1 + (u - job.row_prefix[lo]);
-            o = ia * job.A.n - ia * (ia + 1) / 2 + (jb - ia - 1);
+            o = ia * job.A.n - ia * (ia + 1) / 2 + (jb - ia - 1) - job.out_base;
         } else {
             const uint64_t r = u / nb;
             ia = job.rows ? (uint64_t)job.rows[r] : job.a0 + r;

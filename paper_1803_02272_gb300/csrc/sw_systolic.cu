@@ -459,7 +459,7 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
                             if (J.mode == OUT_TRI) {
                                 const uint64_t i = min((uint64_t)u.q, (uint64_t)so);
                                 const uint64_t j = max((uint64_t)u.q, (uint64_t)so);
-                                idx = i * J.n - i * (i + 1) / 2 + (j - i - 1);
+                                idx = i * J.n - i * (i + 1) / 2 + (j - i - 1) - J.out_base;
                             } else {
                                 idx = ((uint64_t)u.q - J.row0) * J.ld + ((uint64_t)so - J.col0);
                             }

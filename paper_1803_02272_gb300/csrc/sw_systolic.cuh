@@ -21,6 +21,7 @@ struct SysJob {
     int conversion;
     int gap_open;               // affine gaps (extend 1) when > 0; launch with affine = true
     uint64_t out_len;           // entries of out (checked in bounds-checked builds)
+    uint64_t out_base;          // OUT_TRI: out[k(i,j) - out_base] (a band of rows); 0 otherwise
 };
 
 // One query (original index q in Q, length <= 512) against the subjects at list

@@ -34,7 +34,7 @@ EXPORTS = [
     "gbd_server_wait", "gbd_server_destroy", "gbd_last_error", "gbd_probe_op_rate",
     "gbd_kernel_launches", "gbd_tile_noalloc", "gbd_sqdist_square", "gbd_gram_apply", "gbd_mds",
     "gbd_tile_hits", "gbd_threshold_components", "gbd_tri_components", "gbd_batch_tuning",
-    "gbd_rect_hits", "gbd_bounds_check", "gbd_debug_output_limit",
+    "gbd_rect_hits", "gbd_bounds_check", "gbd_debug_output_limit", "gbd_all_pairs_to_host",
 ]
 
 
@@ -72,6 +72,7 @@ def _declare(lib):
         "gbd_set_max_len": ([vp], u32),
         "gbd_set_pair_cells": ([vp], ctypes.c_double),
         "gbd_all_pairs": ([vp, vp, vp, u64, vp], ci),
+        "gbd_all_pairs_to_host": ([vp, vp, vp, u64, u64, vp], ci),
         "gbd_tile": ([vp, vp, u64, u64, vp, u64, u64, vp, u64, vp], ci),
         "gbd_batch": ([vp, vp, u64, vp, vp], ci),
         "gbd_server_create": ([vp, vp, pp], ci),
@@ -192,6 +193,11 @@ def gbd_set_pair_cells(s: int) -> float:
 
 def gbd_all_pairs(ctx: int, s: int, d_tri, tri_len: int, stream=None) -> None:
     _check(_lib.gbd_all_pairs(ctx, s, _ptr(d_tri), tri_len, _stream(stream)))
+
+
+def gbd_all_pairs_to_host(ctx: int, s: int, h_tri, tri_len: int, band_entries: int = 0, stream=None) -> None:
+    """The triangle into host memory (a numpy array or a pinned torch tensor), band by band."""
+    _check(_lib.gbd_all_pairs_to_host(ctx, s, _ptr(h_tri), tri_len, band_entries, _stream(stream)))
 
 
 def gbd_tile(ctx: int, A: int, a0: int, a1: int, B: int, b0: int, b1: int, d_out, ld: int,

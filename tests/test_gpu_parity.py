@@ -433,3 +433,39 @@ def test_conversions_tile_and_batch_exact(gbd, conv):
     torch.cuda.synchronize()
     for x, o in zip(samples, outs):
         np.testing.assert_array_equal(gbd.as_uint16(o), oracle.all_pairs(x, conversion=co))
+
+
+@pytest.mark.parametrize("kernel", ["auto", "general"])
+def test_all_pairs_to_host_bands_exact(gbd, kernel):
+    """The triangle computed band by band into host memory: many small bands (a few rows
+    each, both staging buffers reused many times), one band, and reads longer than 512
+    bases (general-kernel rows inside the bands); equal to the oracle and to the device
+    triangle of gbd_all_pairs."""
+    ctx = _ctx(gbd, kernel)
+    for rs in (synth.workload_plain_small(), synth.from_strings(_edge_reads())):
+        s = ctx.load(rs)
+        m = rs.n * (rs.n - 1) // 2
+        want = oracle.all_pairs(rs)
+        for band in (rs.n - 1, 700, 0):
+            host = np.full(m, 0xFFFF, dtype=np.uint16)
+            gbd.gbd_all_pairs_to_host(ctx.handle, s.handle, host, m, band)
+            np.testing.assert_array_equal(host, want)
+        np.testing.assert_array_equal(_all_pairs(gbd, ctx, rs), want)
+
+
+def test_all_pairs_to_host_pinned_10k(gbd):
+    """10^4 reads into a page-locked host triangle with 2^22-entry bands (twelve bands):
+    identical to the device triangle."""
+    import torch
+    rs = synth.workload_plain_10k()
+    ctx = _ctx(gbd)
+    s = ctx.load(rs)
+    m = rs.n * (rs.n - 1) // 2
+    host = torch.empty(m, dtype=torch.int16, pin_memory=True)
+    gbd.gbd_all_pairs_to_host(ctx.handle, s.handle, host, m, 1 << 22)
+    dev = gbd.as_uint16(ctx.all_pairs(s))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(host.numpy().view(np.uint16), dev)
+    with pytest.raises(gbd.GbdError) as ei:
+        gbd.gbd_all_pairs_to_host(ctx.handle, s.handle, host, m - 1, 0)
+    assert ei.value.code == gbd.GBD_EINVAL
