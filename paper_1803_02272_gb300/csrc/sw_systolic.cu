@@ -18,8 +18,9 @@
 //    alignment), i.e. one __viaddmax_s16x2 and one __vimax3_s16x2 per two cells.
 //  * s + 2 comes from a score profile in shared memory: for each query base q and
 //    stream column j, SP[q][j] = (s(q, b_lo[j]) + 2, s(q, b_hi[j]) + 2) as int16x2, or a
-//    large negative value where the column is padding.  The profile is a ring of 36
-//    chunks of 16 columns, refilled one chunk ahead by the whole warp; each lane reads
+//    large negative value where the column is padding.  The profile is a ring of 48
+//    chunks of 16 columns, refilled one chunk ahead by the whole warp with one byte
+//    permutation per word (the selectors are built once per 16 chunks); each lane reads
 //    it with 64-bit loads two steps at a time (a row's column advances by one per step).
 //  * Subjects start on 16-column chunk boundaries (a subject's 2-bit packed word = one
 //    chunk).  At a subject's first column, a row's left and diagonal inputs are reset to
@@ -55,7 +56,10 @@ constexpr int PWORDS = (SLOTS + 2 * (SLOTS / 16) + 31) & ~31;
 constexpr int NARR = 4;                      // per-warp profiles for A, C, G, T
 constexpr int TABLE_WORDS = RING_CHUNKS * 4; // per chunk: 4 words of stream metadata
 constexpr int TABLE_OFF = NARR * PWORDS;
-constexpr int WARP_WORDS = TABLE_OFF + TABLE_WORDS;
+// Profile selectors of the 16 chunks described last: per chunk 16 columns x 16 bits
+constexpr int SEL_WORDS = 16 * 8;
+constexpr int SEL_OFF = TABLE_OFF + TABLE_WORDS;
+constexpr int WARP_WORDS = SEL_OFF + SEL_WORDS;
 constexpr int WARPS_PER_BLOCK = 2;
 constexpr uint32_t NEG2 = 0xC000C000u;       // (-16384, -16384)
 constexpr int C0 = 1536;                     // floor offset: f >= ~1000 for every lane
@@ -64,7 +68,8 @@ constexpr int REBASE_CHUNKS = 512;           // 8192 steps
 constexpr uint32_t REBASE2 = 0x20002000u;    // 8192 in both halves
 static_assert(PWORDS % 32 == 0, "profile arrays are 128-byte aligned");
 static_assert((REBASE_CHUNKS & (REBASE_CHUNKS - 1)) == 0, "rebase period is a power of two");
-static_assert(TABLE_OFF % 4 == 0 && WARP_WORDS % 32 == 0, "table and warp regions stay bank-aligned");
+static_assert(TABLE_OFF % 4 == 0 && SEL_OFF % 32 == 0 && WARP_WORDS % 32 == 0,
+              "table, selector and warp regions stay bank-aligned");
 // One never-matching profile per block serves the query rows past a read's end.
 constexpr int NEG_OFF = WARPS_PER_BLOCK * WARP_WORDS;
 constexpr int BLOCK_WORDS = NEG_OFF + PWORDS;
@@ -106,7 +111,16 @@ struct SysUnit {
 // describes the next 16 chunks of both halves at once: lane t of half h (lanes 0-15:
 // h = 0, lanes 16-31: h = 1) works out chunk 16b + t of half h from the subject lengths
 // by a prefix sum over the half's lanes, writes the chunk's metadata into the table, and
-// keeps the chunk's packed word and valid-column count for the profile refill.
+// writes the chunk's profile selectors (below) for the refill.
+//
+// Profile selectors.  The profile word of query base q and column x is the byte
+// permutation of T_q = (bytes c = 0..3: 3 if c == q else 1, i.e. s(q, c) + 2) and
+// Y = 0x0000C000 that the column's 16-bit selector picks: per half, a selector byte
+// 0x60 | code takes T_q's byte `code` and a zero high byte (s + 2 as int16), and 0x54 (a
+// column past the subject's end) takes 0x00 and 0xC0 (the never-matching -16384).  The
+// selector bytes of four columns are built at once from the packed word, and the two
+// halves of a column are interleaved (low half's byte, then high half's) so that a column's
+// selector is one 16-bit word.
 struct HalfCursor {
     uint32_t pos;      // list position (within the half) of the subject of chunk 16b
     uint32_t ck;       // chunk of that subject
@@ -117,8 +131,7 @@ struct HalfCursor {
 // table slot of chunk b16; b16 is a multiple of 16, so tslot + t never wraps).  Sets C to
 // the first chunk where both halves are padding, once such a chunk appears.
 __device__ __forceinline__ void describe_chunks(const SysJob &J, const SysUnit &u, int lane, HalfCursor &hc,
-                                                uint32_t b16, int tslot, uint32_t *table, uint32_t &word,
-                                                uint32_t &nvpair, int &C)
+                                                uint32_t b16, int tslot, uint32_t *table, uint32_t *sel, int &C)
 {
     const uint32_t t = lane & 15, h = lane >> 4;
     // the subject t positions after the current one
@@ -153,15 +166,38 @@ __device__ __forceinline__ void describe_chunks(const SysJob &J, const SysUnit &
     const bool first = valid && ckt == 0;
     const bool last = valid && rem <= 16u;
     const uint32_t nv = valid ? min(16u, rem) : 0u;
-    word = valid ? __ldg(J.S.words + (uint64_t)sorig * J.S.stride + ckt) : 0u;
+    const uint32_t word = valid ? __ldg(J.S.words + (uint64_t)sorig * J.S.stride + ckt) : 0u;
+    // selector bytes of this half: byte i of B[j] belongs to column 4j + i
+    {
+        const uint32_t wm = nv >= 16u ? word : (word & ((1u << (2u * nv)) - 1u));   // past-end codes 0
+        const uint32_t nvb = nv * 0x01010101u;
+        uint32_t B[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t y = (wm >> (8 * j)) & 0xffu;              // codes of columns 4j..4j+3
+            const uint32_t v = (y | (y << 12)) & 0x000f000fu;        // two columns per 16 bits
+            const uint32_t c = (v | (v << 6)) & 0x03030303u;         // one column per byte
+            // 0x80 + column - nv per byte (no borrow: it stays in [0x70, 0x8f]); bit 7 = past the end
+            const uint32_t past = (((0x80808080u + 0x04040404u * (uint32_t)j + 0x03020100u) - nvb) >> 7) & 0x01010101u;
+            B[j] = c ^ (past * 0x34u) ^ 0x60606060u;                 // 0x60 | code, or 0x54
+        }
+        // interleave with the other half's bytes: the low half's lanes keep columns 4j, 4j+1,
+        // the high half's 4j+2, 4j+3, as word 2j + h of the chunk's 8 (selector slot t)
+        const uint32_t perm = h ? 0x3726u : 0x5140u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t other = __shfl_xor_sync(0xffffffffu, B[j], 16);
+            const int wi = 8 * (int)t + 2 * j + (int)h;
+            if (bounds_ok((uint64_t)wi, SEL_WORDS, BOUNDS_SYSTOLIC_RING)) sel[wi] = __byte_perm(B[j], other, perm);
+        }
+    }
     // the table entry of chunk b16 + t joins both halves: exchange with lane t ^ 16
-    const uint32_t fa = (first ? 1u : 0u) | (last ? 2u : 0u) | (nv << 2);
+    const uint32_t fa = (first ? 1u : 0u) | (last ? 2u : 0u);
     const uint32_t fb = (valid ? slen : 0u) | (p << 16);
     const uint32_t ga = __shfl_xor_sync(0xffffffffu, fa, 16);
     const uint32_t gb = __shfl_xor_sync(0xffffffffu, fb, 16);
     const uint32_t alo = h ? ga : fa, ahi = h ? fa : ga;
     const uint32_t blo = h ? gb : fb, bhi = h ? fb : gb;
-    nvpair = (alo >> 2) | ((ahi >> 2) << 8);
     if (h == 0) {
         uint4 e;
         e.x = ((alo & 1u) ? 0x0000ffffu : 0u) | ((ahi & 1u) ? 0xffff0000u : 0u);
@@ -183,30 +219,33 @@ __device__ __forceinline__ void describe_chunks(const SysJob &J, const SysUnit &
 }
 
 // Write chunk X of the two half streams into the warp's profile ring (slot m = X mod
-// RING_CHUNKS).  Both halves at once: the two base codes of this lane's column sit in the
-// halves of one word, a half equal to the query base q gives s + 2 = 3, any other 1, a
-// padding column the never-matching value.  nvpair = valid columns of the low half |
-// those of the high half << 8.
-__device__ __forceinline__ void fill_chunk(uint32_t *ws, int lane, int m, uint32_t wlo, uint32_t whi,
-                                           uint32_t nvpair)
+// RING_CHUNKS) from its selectors (selector slot X mod 16): lane x and lane x + 16 take
+// column x, the first for bases A and C, the second for G and T.  Ring slot rho = 16m + x
+// sits at padded word pslot(rho) = 18(m + 1) + x; slots 0 and 1 are also written one ring
+// length on, slot RING_CHUNKS - 1 one ring length back.
+__device__ __forceinline__ void fill_chunk(uint32_t *ws, int lane, int m, int slot, const uint32_t (&Tq)[2])
 {
     const int x = lane & 15;
-    const int qa = (lane >> 4) * 2;
-    const uint32_t codes = ((wlo >> (2 * x)) & 3u) | (((whi >> (2 * x)) & 3u) << 16);
-    const uint32_t pad = ((uint32_t)x < (nvpair & 0xffu) ? 0u : 0x0000ffffu) |
-                         ((uint32_t)x < (nvpair >> 8) ? 0u : 0xffff0000u);
-    const int rho = 16 * m + x;
+    const uint32_t q = (uint32_t)(lane >> 4) * 2u;
+    const int si = 16 * slot + x;
+    uint32_t sel = 0x5454u;
+    if (bounds_ok((uint64_t)si, 2 * SEL_WORDS, BOUNDS_SYSTOLIC_RING))
+        sel = reinterpret_cast<const uint16_t *>(ws + SEL_OFF)[si];
+    const int w = 18 * m + 18 + x;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
-        const uint32_t q = (uint32_t)(qa + t);
-        const uint32_t ne = __vminu2(codes ^ (q * ONE2), ONE2);   // 0 where the base matches, else 1
-        const uint32_t v = lop_sel(0x00030003u - ne - ne, NEG2, pad);
-        uint32_t *arr = ws + q * PWORDS;
-        if (bounds_ok(pslot(rho), PWORDS, BOUNDS_SYSTOLIC_RING)) arr[pslot(rho)] = v;
-        if (rho < 32 && bounds_ok(pslot(rho + RING), PWORDS, BOUNDS_SYSTOLIC_RING)) arr[pslot(rho + RING)] = v;
-        if (rho >= RING - 16 && bounds_ok(pslot(rho - RING), PWORDS, BOUNDS_SYSTOLIC_RING)) arr[pslot(rho - RING)] = v;
+        const uint32_t v = __byte_perm(Tq[t], 0x0000C000u, sel);
+        uint32_t *arr = ws + (q + (uint32_t)t) * PWORDS;
+        if (bounds_ok((uint64_t)w, PWORDS, BOUNDS_SYSTOLIC_RING)) arr[w] = v;
+        if (m < 2 && bounds_ok((uint64_t)(w + 18 * RING_CHUNKS), PWORDS, BOUNDS_SYSTOLIC_RING))
+            arr[w + 18 * RING_CHUNKS] = v;
+        if (m == RING_CHUNKS - 1 && bounds_ok((uint64_t)(w - 18 * RING_CHUNKS), PWORDS, BOUNDS_SYSTOLIC_RING))
+            arr[w - 18 * RING_CHUNKS] = v;
     }
 }
+static_assert(pslot(16 * 5 + 7) == 18 * 6 + 7 && pslot(16 * RING_CHUNKS + 15) == 18 * (RING_CHUNKS + 1) + 15 &&
+              pslot(-16) == 0 && pslot(16 * 1 + 15 + RING) == 18 * (1 + 1) + 15 + 18 * RING_CHUNKS,
+              "ring slot 16m + x sits at padded word 18(m + 1) + x");
 
 __device__ __forceinline__ uint2 lds64(const uint32_t *ws_words, uint32_t byte_off)
 {
@@ -229,11 +268,14 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
     hc.ck = 0;
     hc.cnt = (u.nsub + 1 - (uint32_t)(lane >> 4)) >> 1;   // half h: list positions h, h+2, ...
     uint32_t *const table = ws + TABLE_OFF;
-    uint32_t dword, dnv;                       // this lane's chunk of the current 16
-    int tslot = 0;                             // table slot of the first of those chunks
-    describe_chunks(J, u, lane, hc, 0u, 0, table, dword, dnv, C);
-    fill_chunk(ws, lane, 0, __shfl_sync(0xffffffffu, dword, 0), __shfl_sync(0xffffffffu, dword, 16),
-               __shfl_sync(0xffffffffu, dnv, 0));
+    uint32_t *const sel = ws + SEL_OFF;
+    int tslot = 0;                             // table slot of the first of the 16 chunks
+    // T_q of this lane's two base codes (lanes 0-15: codes 0 and 1; lanes 16-31: 2 and 3)
+    const uint32_t Tq[2] = {0x01010101u + (2u << (16u * (uint32_t)(lane >> 4))),
+                            0x01010101u + (0x200u << (16u * (uint32_t)(lane >> 4)))};
+    describe_chunks(J, u, lane, hc, 0u, 0, table, sel, C);
+    __syncwarp();
+    fill_chunk(ws, lane, 0, 0, Tq);
     __syncwarp();
 
     // ---- per-row profile addresses
@@ -336,13 +378,10 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
             // g+1 starts them; g+1 is odd for the first chunk of the pair)
             if ((PAIR == 1 || h2 == 1) && ((g + 1) & 15) == 0) {
                 tslot = (tslot == RING_CHUNKS - 16) ? 0 : tslot + 16;
-                describe_chunks(J, u, lane, hc, (uint32_t)(g + 1), tslot, table, dword, dnv, C);
+                describe_chunks(J, u, lane, hc, (uint32_t)(g + 1), tslot, table, sel, C);
+                __syncwarp();
             }
-            {
-                const int src = (g + 1) & 15;
-                fill_chunk(ws, lane, m_fill, __shfl_sync(0xffffffffu, dword, src),
-                           __shfl_sync(0xffffffffu, dword, src + 16), __shfl_sync(0xffffffffu, dnv, src));
-            }
+            fill_chunk(ws, lane, m_fill, (g + 1) & 15, Tq);
             m_fill = (m_fill == RING_CHUNKS - 1) ? 0 : m_fill + 1;
             __syncwarp();
 
