@@ -273,6 +273,12 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
     // T_q of this lane's two base codes (lanes 0-15: codes 0 and 1; lanes 16-31: 2 and 3)
     const uint32_t Tq[2] = {0x01010101u + (2u << (16u * (uint32_t)(lane >> 4))),
                             0x01010101u + (0x200u << (16u * (uint32_t)(lane >> 4)))};
+    // Lane k meets chunks -k..-1 (before the stream reaches it) in table slots 48-k..47;
+    // the describes first overwrite those slots after every lane has left them (slots
+    // 16..31 when chunk 16 is refilled, 32..47 at chunk 32).  Their entry starts no subject
+    // and ends one in both halves, so that each lane's chunk 0 begins with a cleared maximum.
+#pragma unroll
+    for (int w = 16 * 4 + lane; w < RING_CHUNKS * 4; w += 32) table[w] = ((w & 3) == 1) ? 0xffffffffu : 0u;
     describe_chunks(J, u, lane, hc, 0u, 0, table, sel, C);
     __syncwarp();
     fill_chunk(ws, lane, 0, 0, Tq);
@@ -323,7 +329,7 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
     const uint32_t ngo = AFFINE ? pack2(-(int)J.gap_open) : 0u;
     uint32_t up0_prev = f_prev2;               // row 0's diagonal input
     uint32_t curRel = 0, prevRel = 0, acc = 0, emit = 0;
-    uint32_t Mlast_prev = 0;                   // "ends a subject" masks of chunk c-1
+    uint32_t Mlast_prev = 0xffffffffu;         // "ends a subject" masks of chunk c-1
     uint32_t lens_prev = 0, pos_prev = 0;
     uint2 sp[R];
 #pragma unroll
@@ -387,15 +393,9 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
 
             // ---- this lane's chunk c: stream metadata
             const int c = g - lane;
-            uint32_t Mfirst = 0, Mend;                 // Mend: chunk c-1 ended a subject
-            uint32_t lens_c = 0, pos_c = 0, Mlast_c = 0;
-            if (c >= 0) {
-                const uint32_t *e = table + 4 * (h2 ? m_c1 : m_c);
-                const uint4 ev = *reinterpret_cast<const uint4 *>(e);
-                Mfirst = ev.x; Mlast_c = ev.y; lens_c = ev.z;
-                pos_c = ev.w;
-            }
-            Mend = (c >= 1) ? Mlast_prev : 0xffffffffu;   // c <= 0: discard what came before
+            const uint4 ev = *reinterpret_cast<const uint4 *>(table + 4 * (h2 ? m_c1 : m_c));
+            const uint32_t Mfirst = ev.x, Mlast_c = ev.y, lens_c = ev.z, pos_c = ev.w;
+            const uint32_t Mend = Mlast_prev;            // chunk c-1 ended a subject (c <= 0: all ones)
             const uint32_t fbase = f_prev + ONE2;         // floor at step 0 of this chunk
 
             // ---- 16 steps
@@ -507,7 +507,7 @@ __device__ __forceinline__ void run_unit(const SysJob &J, const SysUnit &u, uint
                         }
                     }
                 }
-                Mlast_prev = (c >= 0) ? Mlast_c : 0u;
+                Mlast_prev = Mlast_c;
                 lens_prev = lens_c;
                 pos_prev = pos_c;
             }
